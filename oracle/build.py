@@ -1,0 +1,29 @@
+"""Compile the FP64 oracle (``oracle.c``) into ``oracle/liboracle.so`` with gcc.
+
+Test infrastructure: the oracle is the slow, plain reference the GPU solver is
+checked against; building it does not put it on any product path.
+"""
+import subprocess
+import sys
+from pathlib import Path
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "oracle.c"
+LIB = HERE / "liboracle.so"
+
+
+def build(force: bool = False) -> Path:
+    if force or not LIB.exists() or LIB.stat().st_mtime < SRC.stat().st_mtime:
+        tmp = LIB.with_suffix(".so.tmp")
+        r = subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-Wall",
+                            "-o", str(tmp), str(SRC), "-lm"],
+                           stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout)
+            raise RuntimeError("oracle build failed")
+        tmp.replace(LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
