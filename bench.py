@@ -1,0 +1,337 @@
+"""Benchmark: fluid-site MLUPS and HBM GB/s of the fused D3Q19 step on GB300.
+
+Workload (one GPU): the seeded depth-6 bifurcating vessel tree, ~20M fluid
+sites (seed 2202, Murray radii, 30-70 degree bifurcations, 64 pressure
+outlets), tau = 0.55, pulsatile inlet u(t) = 0.02 (1 + 0.5 cos(2 pi t/2000))
+with a parabolic cross-section weight, rho = 1 at every outlet.  Inputs are
+synthetic and seeded; the paper's patient geometries are not available.
+
+One benchmark step = one LB time step over the whole lattice = one launch of
+the fused stream-collide-boundary kernel.  ``value`` is MLUPS (Eq. 9 of arXiv
+2202.11770) with the lattice resident in HBM; the state (~4.5 GB touched per
+step) is far larger than L2, so no flush is needed between steps.
+
+``--gpus N`` (under torchrun) runs N independent replicas, one per GPU
+(the single-GPU solver does not shard); ``value`` sums the ranks' site
+updates over the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure, plain C,
+one thread) on the same lattice: a bounded number of full-lattice steps.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "fluid-site MLUPS and HBM GB/s (% of peak), FP32 vs 16-bit store; adjoint/fwd"
+WORKLOAD = "seeded depth-6 vessel tree, 20M fluid sites, D3Q19 LBGK tau=0.55, pulsatile Ladd inlet, 64 pressure outlets"
+
+# Algorithmic bytes per site update of the pull A-B step: 19 populations read
+# + 19 written (storage precision) + the int32 streaming-index table
+# (18 x 4 B).  Boundary-link records are O(boundary sites) and not counted.
+def bytes_per_site(elem: int) -> int:
+    return 19 * elem * 2 + 18 * 4
+
+
+# DRAM traffic of the FP32 step kernel from one ncu capture
+# (profiles/ncu_k_step_fp32_tree.md), per site update, valid only while the
+# kernel sources are unchanged (SHA-256 of the files below).
+TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
+TRAFFIC = {"sha": None, "bytes_per_site": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in TRAFFIC_FILES:
+        h.update((ROOT / f).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, v in enumerate(flags) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def tree_lattice(target):
+    from paper_2202_11770_gb300 import geometry
+    return geometry.tree(6, 2202, target_sites=target, length_ratio=5.0)
+
+
+def set_bc(x, lat):
+    x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 2000.0})
+    for k in range(1, len(lat.iolets)):
+        x.set_pressure(k, 1.0)
+
+
+def time_form(lat, precision, steps, warmup, torch, dist=None):
+    from paper_2202_11770_gb300 import hemegb
+    s = hemegb.Solver(lat, tau=0.55, precision=precision)
+    set_bc(s, lat)
+    s.init_equilibrium()
+    s.step(warmup)
+    stream = s.stream
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mass, _ = s.reduce()
+    assert math.isfinite(mass)
+    del s
+    torch.cuda.empty_cache()
+    return ms
+
+
+def e2e_job(lat, steps, torch):
+    """Whole job through the public API from host buffers: create (lattice
+    tables uploaded from pinned host memory), init, `steps` steps with the
+    density and velocity read back to host every 100 steps (the paper's
+    property-cache interval) and a final FP64 reduction."""
+    from paper_2202_11770_gb300 import hemegb
+    from paper_2202_11770_gb300.geometry import Lattice
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    lat_p = Lattice(xyz=pin(lat.xyz), src=pin(lat.src), type=lat.type, wall_normal=pin(lat.wall_normal),
+                    amp_group=pin(lat.amp_group), iolets=lat.iolets, info=lat.info)
+    n = lat.n
+    rho_h = torch.empty(n, dtype=torch.float32).pin_memory().numpy()
+    u_h = torch.empty(3 * n, dtype=torch.float32).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = hemegb.Solver(lat_p, tau=0.55, precision="fp32")
+    set_bc(s, lat_p)
+    s.init_equilibrium()
+    reads = 0
+    for k in range(steps // 100):
+        s.step(100)
+        hemegb.hlb_read_macros(s.handle, rho_h.ctypes.data, u_h.ctypes.data, None, hemegb.HLB_HOST)
+        reads += 1
+    s.step(steps % 100)
+    mass, flux = s.reduce()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = lat.xyz.nbytes + lat.src.nbytes + lat.wall_normal.nbytes + lat.amp_group.nbytes
+    h2d_step = h2d / steps + 2096          # lattice upload amortised + per-launch boundary parameters
+    d2h_step = reads * (rho_h.nbytes + u_h.nbytes) / steps + 8 * (1 + len(lat.iolets)) / steps
+    del s
+    torch.cuda.empty_cache()
+    return n * steps / dt / 1e6, h2d_step, d2h_step
+
+
+def cpu_baseline(lat, steps):
+    import oracle
+    o = oracle.Oracle(lat, tau=0.55)
+    set_bc(o, lat)
+    o.init_equilibrium()
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return lat.n * steps / dt / 1e6, dt
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    lat = tree_lattice(args.sites)
+    w = min(args.warmup, 1)
+    k = max(1, min(args.steps, args.ref_steps))
+    import oracle
+    o = oracle.Oracle(lat, tau=0.55)
+    set_bc(o, lat)
+    o.init_equilibrium()
+    o.step(w)
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    v = lat.n * k / dt / 1e6
+    sample = f"{k} full-lattice steps of the {lat.n}-site tree after {w} warm-up step(s), FP64 oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": k, "warmup": w, "ms_per_step": dt / k * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_sites": lat.n},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    else:
+        torch.cuda.set_device(0)
+    from paper_2202_11770_gb300 import hemegb
+    hemegb.library()
+
+    lat = tree_lattice(args.sites)
+    n = lat.n
+    peak, peak_kind = measured_peaks()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_form(lat, "fp32", args.steps, args.warmup, torch, dist)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_updates = n * args.steps * world
+    value = total_updates / (ms * 1e-3) / 1e6
+    per_launch_s = ms * 1e-3 / args.steps
+    alg = bytes_per_site(4) * n
+    achieved = alg / per_launch_s / 1e9
+    traffic = None
+    if TRAFFIC["sha"] == kernel_sha() and TRAFFIC["bytes_per_site"]:
+        traffic = TRAFFIC["bytes_per_site"] * n
+
+    forms = {}
+    if not args.quick:
+        for prec in ("bf16", "fp16"):
+            msf = time_form(lat, prec, args.steps, args.warmup, torch, dist)
+            gbs = bytes_per_site(2) * n / (msf * 1e-3 / args.steps) / 1e9
+            forms[prec] = {"mlups": n * args.steps / (msf * 1e-3) / 1e6, "ms_per_step": msf / args.steps,
+                           "gbs": gbs, "frac_of_measured_peak": gbs / peak, "bytes_per_site": bytes_per_site(2)}
+        forms["fp32"] = {"mlups": n * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
+                         "gbs": achieved, "frac_of_measured_peak": achieved / peak,
+                         "bytes_per_site": bytes_per_site(4)}
+
+    e2e = None
+    if not args.quick:
+        v, h2d, d2h = e2e_job(lat, args.e2e_steps, torch)
+        e2e = {"value": v * world, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "job": f"create + init + {args.e2e_steps} steps + host readback of rho,u every 100 steps"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt = cpu_baseline(lat, args.cpu_steps)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_steps} full-lattice steps of the {n}-site tree ({dt:.1f} s), FP64 oracle, 1 thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_sites": n, "tau": 0.55, "scheme": "pull A-B",
+                       "parallelism": f"replicas x{world}", "l2": "working set 4.5 GB/step >> 129 MB L2, no flush",
+                       "fill": round(lat.info["fill"], 4)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": "k_step<float,gather>", "algorithmic_bytes_per_site": bytes_per_site(4)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": args.steps,
+            "forms": forms,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sites", type=int, default=20_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=2000)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--ref-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="FP32 only, no e2e (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

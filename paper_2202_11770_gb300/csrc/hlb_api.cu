@@ -1,0 +1,478 @@
+// hlb_api.cu — C ABI of libhemegb: validation, workspace layout, set-up of
+// the device tables (the GPU initialisation of arXiv 2202.11770,
+// Section 3.2.1), time bookkeeping and readback.  All compute runs in the
+// kernels of hlb_forward.cu / hlb_adjoint.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hlb_internal.h"
+
+using namespace hlb;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+int hlb_fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int hlb_cuda_fail(cudaError_t e, const char* where) {
+  return hlb_fail(HLB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CUDA_TRY(expr)                                     \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return hlb_cuda_fail(_e, #expr); \
+  } while (0)
+
+extern "C" const char* hlb_last_error(void) { return g_err.c_str(); }
+extern "C" int hlb_version(void) { return 10000; }
+
+// ---------------------------------------------------------------------------
+// waveforms
+// ---------------------------------------------------------------------------
+double HostWave::at(double t) const {
+  if (kind == HLB_WAVE_CONST) return mean;
+  if (kind == HLB_WAVE_COSINE) return mean * (1.0 + rel * cos(2.0 * M_PI * t / period + phase));
+  double x = fmod(t, period);
+  if (x < 0) x += period;
+  const int ns = (int)samples.size();
+  double pos = x / period * ns;
+  int j = (int)floor(pos);
+  double fr = pos - j;
+  j %= ns;
+  return mean * ((1.0 - fr) * samples[j] + fr * samples[(j + 1) % ns]);
+}
+
+static int parse_wave(const hlb_waveform* w, HostWave* out) {
+  if (!w) return hlb_fail(HLB_ERR_ARG, "null waveform");
+  HostWave hw;
+  hw.kind = w->kind;
+  hw.mean = w->mean;
+  hw.rel = w->rel_amp;
+  hw.period = w->period;
+  hw.phase = w->phase;
+  if (w->kind != HLB_WAVE_CONST && w->kind != HLB_WAVE_COSINE && w->kind != HLB_WAVE_TABLE)
+    return hlb_fail(HLB_ERR_ARG, "unknown waveform kind");
+  if (w->kind != HLB_WAVE_CONST && !(w->period > 0)) return hlb_fail(HLB_ERR_ARG, "waveform period must be > 0");
+  if (w->kind == HLB_WAVE_TABLE) {
+    if (w->n_samples < 1 || !w->samples) return hlb_fail(HLB_ERR_ARG, "table waveform needs samples");
+    hw.samples.assign(w->samples, w->samples + w->n_samples);
+  }
+  if (!std::isfinite(hw.mean)) return hlb_fail(HLB_ERR_ARG, "non-finite waveform mean");
+  *out = hw;
+  return HLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solver helpers
+// ---------------------------------------------------------------------------
+size_t hlb_solver::elem_bytes() const {
+  switch (precision) {
+    case HLB_FP32: return 4;
+    case HLB_BF16: return 2;
+    case HLB_FP16: return 2;
+    default: return 8;
+  }
+}
+
+StepParams hlb_solver::params(int64_t tb) const {
+  StepParams p;
+  memset(&p, 0, sizeof p);
+  p.n = n;
+  p.omega = (float)(1.0 / tau);
+  p.n_iolets = n_iolets;
+  p.ladd_rho_one = ladd_rho_one;
+  p.ghost_full_u = ghost_full_u;
+  for (int k = 0; k < n_iolets; ++k) {
+    p.io[k].nx = (float)iolets[k].normal[0];
+    p.io[k].ny = (float)iolets[k].normal[1];
+    p.io[k].nz = (float)iolets[k].normal[2];
+    double w = wave[k].at((double)tb);
+    p.io[k].val = (float)(iolets[k].kind == HLB_VELOCITY ? w : w - 1.0);
+  }
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// lattice validation and workspace layout
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Layout {
+  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, total = 0;
+  int64_t n_links = 0;
+  int32_t n_groups = 0;
+};
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* per_iolet_links) {
+  if (!L || !o) return hlb_fail(HLB_ERR_ARG, "null lattice or options");
+  if (L->n_sites < 1 || L->n_sites >= ((int64_t)1 << 31)) return hlb_fail(HLB_ERR_ARG, "n_sites must be in [1, 2^31)");
+  if (!L->src || !L->xyz) return hlb_fail(HLB_ERR_ARG, "lattice needs xyz and src");
+  if (L->n_iolets < 0 || L->n_iolets > HLB_MAX_IOLETS) return hlb_fail(HLB_ERR_ARG, "n_iolets out of range");
+  if (L->n_iolets > 0 && !L->iolets) return hlb_fail(HLB_ERR_ARG, "null iolet array");
+  if (o->precision < HLB_FP32 || o->precision > HLB_FP64) return hlb_fail(HLB_ERR_ARG, "unknown precision");
+  if (o->scheme != HLB_SCHEME_AUTO && o->scheme != HLB_PULL_AB && o->scheme != HLB_AA)
+    return hlb_fail(HLB_ERR_ARG, "unknown scheme");
+  if (o->scheme == HLB_AA) return hlb_fail(HLB_ERR_ARG, "scheme HLB_AA is not available in this build");
+  for (int k = 0; k < L->n_iolets; ++k) {
+    const hlb_iolet& io = L->iolets[k];
+    if (io.kind != HLB_VELOCITY && io.kind != HLB_PRESSURE) return hlb_fail(HLB_ERR_ARG, "bad iolet kind");
+    double nn = io.normal[0] * io.normal[0] + io.normal[1] * io.normal[1] + io.normal[2] * io.normal[2];
+    if (!(fabs(nn - 1.0) < 1e-6)) return hlb_fail(HLB_ERR_ARG, "iolet normal must be a unit vector");
+    if (!(io.radius > 0)) return hlb_fail(HLB_ERR_ARG, "iolet radius must be > 0");
+    if (io.n_groups < 1) return hlb_fail(HLB_ERR_ARG, "iolet n_groups must be >= 1");
+  }
+  const int64_t n = L->n_sites;
+  per_iolet_links->assign((size_t)std::max(1, (int)L->n_iolets), 0);
+  for (int i = 1; i < Q; ++i) {
+    const int32_t* row = L->src + (int64_t)(i - 1) * n;
+    for (int64_t x = 0; x < n; ++x) {
+      int32_t s = row[x];
+      if (s >= 0) {
+        if (s >= n) return hlb_fail(HLB_ERR_ARG, "src index out of range");
+      } else if (s <= -2) {
+        int k = -s - 2;
+        if (k >= L->n_iolets) return hlb_fail(HLB_ERR_ARG, "link code names a missing iolet");
+        if (L->iolets[k].kind == HLB_VELOCITY && L->amp_group) {
+          int g = L->amp_group[x];
+          if (g < 0 || g >= L->iolets[k].n_groups) return hlb_fail(HLB_ERR_ARG, "amplitude group out of range");
+        }
+        (*per_iolet_links)[k]++;
+      }
+    }
+  }
+  return HLB_OK;
+}
+
+Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int64_t>& per_iolet) {
+  Layout y;
+  const int64_t n = L->n_sites;
+  size_t eb = o->precision == HLB_FP64 ? 8 : (o->precision == HLB_FP32 ? 4 : 2);
+  size_t state = align_up(eb * 19 * (size_t)n);
+  for (int k = 0; k < L->n_iolets; ++k) y.n_links += per_iolet[k];
+  for (int k = 0; k < L->n_iolets; ++k)
+    if (L->iolets[k].kind == HLB_VELOCITY) y.n_groups += L->iolets[k].n_groups;
+  size_t off = 0;
+  y.f0 = off; off += state;
+  y.f1 = off; off += state;
+  y.src = off; off += align_up(sizeof(int32_t) * 18 * (size_t)n);
+  y.links = off; off += align_up(sizeof(LinkRec) * (size_t)std::max<int64_t>(y.n_links, 1));
+  y.amp = off; off += align_up(sizeof(float) * (size_t)std::max(y.n_groups, 1));
+  y.normal = off; off += L->wall_normal ? align_up(sizeof(float) * 3 * (size_t)n) : 0;
+  y.stage = off; off += align_up(sizeof(float) * 5 * (size_t)n);
+  y.red = off; off += align_up(sizeof(double) * (size_t)hlb_reduce_slots(n, L->n_iolets));
+  y.total = off;
+  return y;
+}
+
+}  // namespace
+
+extern "C" int hlb_workspace_bytes(const hlb_lattice* L, const hlb_options* o, size_t* bytes) {
+  if (!bytes) return hlb_fail(HLB_ERR_ARG, "null output");
+  std::vector<int64_t> per;
+  int rc = validate(L, o, &per);
+  if (rc) return rc;
+  *bytes = layout(L, o, per).total;
+  return HLB_OK;
+}
+
+extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, size_t ws_bytes, hlb_stream stream,
+                          hlb_solver** out) {
+  if (!out) return hlb_fail(HLB_ERR_ARG, "null output");
+  *out = nullptr;
+  std::vector<int64_t> per;
+  int rc = validate(L, o, &per);
+  if (rc) return rc;
+  Layout y = layout(L, o, per);
+  if (!ws) return hlb_fail(HLB_ERR_WS, "null workspace");
+  if (((uintptr_t)ws & 255) != 0) return hlb_fail(HLB_ERR_WS, "workspace must be 256-byte aligned");
+  if (ws_bytes < y.total)
+    return hlb_fail(HLB_ERR_WS, "workspace too small: need " + std::to_string(y.total) + " bytes");
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, ws) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return hlb_fail(HLB_ERR_WS, "workspace is not device memory");
+  }
+
+  hlb_solver* h = new (std::nothrow) hlb_solver();
+  if (!h) return hlb_fail(HLB_ERR_NOMEM, "host allocation failed");
+  const int64_t n = L->n_sites;
+  h->n = n;
+  h->n_iolets = L->n_iolets;
+  h->iolets.assign(L->iolets, L->iolets + L->n_iolets);
+  h->precision = o->precision;
+  h->scheme = HLB_PULL_AB;
+  h->ladd_rho_one = o->ladd_rho_one ? 1 : 0;
+  h->ghost_full_u = o->ghost_full_u ? 1 : 0;
+  h->stream = (cudaStream_t)stream;
+  h->device = attr.device;
+  h->has_normals = L->wall_normal != nullptr;
+  h->wave.resize(h->n_iolets);
+  h->group_offset.assign(h->n_iolets, -1);
+  int32_t g = 0;
+  for (int k = 0; k < h->n_iolets; ++k) {
+    if (h->iolets[k].kind == HLB_VELOCITY) {
+      h->group_offset[k] = g;
+      g += h->iolets[k].n_groups;
+      h->wave[k].mean = 0.0;
+    } else {
+      h->wave[k].mean = 1.0;
+    }
+  }
+  h->n_groups_total = g;
+  h->amp.assign(g, 0.0);
+
+  char* base = (char*)ws;
+  h->f[0] = base + y.f0;
+  h->f[1] = base + y.f1;
+  h->d_src = (int32_t*)(base + y.src);
+  h->d_links = (LinkRec*)(base + y.links);
+  h->d_amp = (float*)(base + y.amp);
+  h->d_normal = L->wall_normal ? (float*)(base + y.normal) : nullptr;
+  h->d_stage = (float*)(base + y.stage);
+  h->d_red = (double*)(base + y.red);
+  h->red_slots = hlb_reduce_slots(n, h->n_iolets);
+
+  // link records sorted by (iolet, group, site, direction)
+  std::vector<int64_t> bucket_base(h->n_iolets + 1, 0);
+  for (int k = 0; k < h->n_iolets; ++k)
+    bucket_base[k + 1] = bucket_base[k] + (h->iolets[k].kind == HLB_VELOCITY ? h->iolets[k].n_groups : 1);
+  std::vector<int64_t> count(bucket_base[h->n_iolets] + 1, 0);
+  auto group_of = [&](int k, int64_t x) -> int {
+    return (h->iolets[k].kind == HLB_VELOCITY && L->amp_group) ? L->amp_group[x] : 0;
+  };
+  for (int64_t x = 0; x < n; ++x)
+    for (int i = 1; i < Q; ++i) {
+      int32_t s = L->src[(int64_t)(i - 1) * n + x];
+      if (s <= -2) count[bucket_base[-s - 2] + group_of(-s - 2, x) + 1]++;
+    }
+  for (size_t b = 1; b < count.size(); ++b) count[b] += count[b - 1];
+  h->n_links = y.n_links;
+  h->link_begin.resize(h->n_iolets + 1);
+  for (int k = 0; k <= h->n_iolets; ++k) h->link_begin[k] = count[bucket_base[k]];
+  std::vector<LinkRec> recs((size_t)std::max<int64_t>(y.n_links, 1));
+  std::vector<int32_t> src(L->src, L->src + (size_t)18 * n);
+  std::vector<int64_t> fillpos(count.begin(), count.end() - 1);
+  for (int64_t x = 0; x < n; ++x)
+    for (int j = 1; j < Q; ++j) {
+      int32_t s = L->src[(int64_t)(j - 1) * n + x];
+      if (s > -2) continue;
+      const int k = -s - 2;
+      const hlb_iolet& io = h->iolets[k];
+      const int gl = group_of(k, x);
+      const int64_t r = fillpos[bucket_base[k] + gl]++;
+      LinkRec& R = recs[r];
+      R.site = (int32_t)x;
+      R.dir = (int8_t)j;
+      R.kind = (int8_t)io.kind;
+      R.iolet = (int16_t)k;
+      R.group = io.kind == HLB_VELOCITY ? h->group_offset[k] + gl : -1;
+      R.coef = 0.f;
+      if (io.kind == HLB_VELOCITY) {
+        // Ladd weight at the link midpoint x - c_j / 2
+        double m[3] = {L->xyz[3 * x] - 0.5 * cx(j), L->xyz[3 * x + 1] - 0.5 * cy(j), L->xyz[3 * x + 2] - 0.5 * cz(j)};
+        double v[3] = {m[0] - io.centre[0], m[1] - io.centre[1], m[2] - io.centre[2]};
+        double sn = v[0] * io.normal[0] + v[1] * io.normal[1] + v[2] * io.normal[2];
+        double r2 = 0;
+        for (int a = 0; a < 3; ++a) {
+          double w = v[a] - sn * io.normal[a];
+          r2 += w * w;
+        }
+        double W = std::max(0.0, 1.0 - r2 / (io.radius * io.radius));
+        double cn = cx(j) * io.normal[0] + cy(j) * io.normal[1] + cz(j) * io.normal[2];
+        // f_j(x) = f'_jbar(x) - 2 w rho (c_jbar . u_w) / cs2 = f'_jbar(x) + 6 w_j rho A W (c_j . n)
+        R.coef = (float)(6.0 * wgt<double>(j) * W * cn);
+      }
+      src[(size_t)(j - 1) * n + x] = -(int32_t)(2 + r);
+    }
+
+  cudaStream_t st = h->stream;
+  int64_t nb = (n + 255) / 256;
+  std::vector<int64_t> begin(h->link_begin);
+  std::vector<float> ampf(std::max(g, 1), 0.f);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * 18 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && y.n_links > 0)
+    e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(float) * ampf.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && h->d_normal)
+    e = cudaMemcpyAsync(h->d_normal, L->wall_normal, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_red + nb, begin.data(), sizeof(int64_t) * begin.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->state_bytes(), st);  // rest: h = f - w = 0
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    delete h;
+    return hlb_cuda_fail(e, "hlb_create upload");
+  }
+  h->cur = 0;
+  h->phase = 0;
+  h->t = 0;
+  *out = h;
+  return HLB_OK;
+}
+
+extern "C" int hlb_destroy(hlb_solver* h) {
+  delete h;
+  return HLB_OK;
+}
+
+extern "C" int hlb_set_stream(hlb_solver* h, hlb_stream s) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  h->stream = (cudaStream_t)s;
+  return HLB_OK;
+}
+
+extern "C" int64_t hlb_n_sites(const hlb_solver* h) { return h ? h->n : -1; }
+extern "C" int hlb_n_amp_groups(const hlb_solver* h) { return h ? h->n_groups_total : -1; }
+
+extern "C" int hlb_set_tau(hlb_solver* h, double tau) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return hlb_fail(HLB_ERR_ARG, "tau must be > 1/2");
+  h->tau = tau;
+  return HLB_OK;
+}
+
+extern "C" int hlb_set_velocity_waveform(hlb_solver* h, int32_t k, const double* amp, int32_t n_groups,
+                                         const hlb_waveform* w) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (k < 0 || k >= h->n_iolets || h->iolets[k].kind != HLB_VELOCITY)
+    return hlb_fail(HLB_ERR_ARG, "not a velocity iolet");
+  if (n_groups != h->iolets[k].n_groups || !amp) return hlb_fail(HLB_ERR_ARG, "amplitude count mismatch");
+  HostWave hw;
+  int rc = parse_wave(w, &hw);
+  if (rc) return rc;
+  for (int gi = 0; gi < n_groups; ++gi)
+    if (!std::isfinite(amp[gi])) return hlb_fail(HLB_ERR_ARG, "non-finite amplitude");
+  h->wave[k] = hw;
+  std::vector<float> af(n_groups);
+  for (int gi = 0; gi < n_groups; ++gi) {
+    h->amp[h->group_offset[k] + gi] = amp[gi];
+    af[gi] = (float)amp[gi];
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->d_amp + h->group_offset[k], af.data(), sizeof(float) * n_groups,
+                           cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return HLB_OK;
+}
+
+extern "C" int hlb_set_pressure(hlb_solver* h, int32_t k, const hlb_waveform* w) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (k < 0 || k >= h->n_iolets || h->iolets[k].kind != HLB_PRESSURE)
+    return hlb_fail(HLB_ERR_ARG, "not a pressure iolet");
+  HostWave hw;
+  int rc = parse_wave(w, &hw);
+  if (rc) return rc;
+  h->wave[k] = hw;
+  return HLB_OK;
+}
+
+extern "C" int hlb_init_equilibrium(hlb_solver* h, double rho0, const float* u0, int32_t where) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (!(rho0 > 0) || !std::isfinite(rho0)) return hlb_fail(HLB_ERR_ARG, "rho0 must be positive");
+  const float* du = u0;
+  if (u0 && where == HLB_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(h->d_stage, u0, sizeof(float) * 3 * (size_t)h->n, cudaMemcpyHostToDevice, h->stream));
+    du = h->d_stage;
+  }
+  CUDA_TRY(hlb_launch_init(h, h->f[0], rho0, du, h->stream));
+  h->cur = 0;
+  h->phase = 0;
+  h->t = 0;
+  if (u0 && where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return HLB_OK;
+}
+
+extern "C" int hlb_step(hlb_solver* h, int64_t nsteps) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (nsteps < 0) return hlb_fail(HLB_ERR_ARG, "negative step count");
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const bool gather = h->phase == 1;
+    CUDA_TRY(hlb_launch_step(h, h->f[h->cur], h->f[h->cur ^ 1], gather, h->t - 1, h->stream));
+    h->cur ^= 1;
+    h->phase = 1;
+    h->t += 1;
+  }
+  return HLB_OK;
+}
+
+extern "C" int hlb_time(const hlb_solver* h, int64_t* t) {
+  if (!h || !t) return hlb_fail(HLB_ERR_ARG, "null argument");
+  *t = h->t;
+  return HLB_OK;
+}
+
+extern "C" int hlb_read_macros(hlb_solver* h, float* rho, float* u, float* wss, int32_t where) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  const int64_t n = h->n;
+  const bool gather = h->phase == 1;
+  if (where == HLB_DEVICE) {
+    CUDA_TRY(hlb_launch_macros(h, h->f[h->cur], gather, h->t - 1, rho, u, wss, h->stream));
+    return HLB_OK;
+  }
+  float* sr = rho ? h->d_stage : nullptr;
+  float* su = u ? h->d_stage + n : nullptr;
+  float* sw = wss ? h->d_stage + 4 * n : nullptr;
+  CUDA_TRY(hlb_launch_macros(h, h->f[h->cur], gather, h->t - 1, sr, su, sw, h->stream));
+  if (rho) CUDA_TRY(cudaMemcpyAsync(rho, sr, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+  if (u) CUDA_TRY(cudaMemcpyAsync(u, su, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
+  if (wss) CUDA_TRY(cudaMemcpyAsync(wss, sw, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return HLB_OK;
+}
+
+extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  const int64_t nb = (h->n + 255) / 256;
+  double* out = h->d_red + nb + (h->n_iolets + 1);
+  CUDA_TRY(hlb_launch_reduce(h, h->f[h->cur], h->phase == 1, h->t - 1, out, h->stream));
+  std::vector<double> host(1 + h->n_iolets);
+  CUDA_TRY(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (mass) *mass = host[0];
+  if (flux)
+    for (int k = 0; k < h->n_iolets; ++k) flux[k] = host[1 + k];
+  if (!std::isfinite(host[0])) return hlb_fail(HLB_ERR_DIVERGED, "mass is not finite");
+  return HLB_OK;
+}
+
+extern "C" int hlb_get_state(hlb_solver* h, void* f, int32_t where, int64_t* t) {
+  if (!h || !f) return hlb_fail(HLB_ERR_ARG, "null argument");
+  const size_t bytes = h->state_bytes();
+  if (h->phase == 0) {
+    CUDA_TRY(cudaMemcpyAsync(f, h->f[h->cur], bytes, where == HLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                             h->stream));
+  } else if (where == HLB_DEVICE) {
+    CUDA_TRY(hlb_launch_state(h, h->f[h->cur], true, h->t - 1, f, h->stream));
+  } else {
+    // the spare population buffer is free until the next step
+    void* spare = h->f[h->cur ^ 1];
+    CUDA_TRY(hlb_launch_state(h, h->f[h->cur], true, h->t - 1, spare, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(f, spare, bytes, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (t) *t = h->t;
+  return HLB_OK;
+}
+
+extern "C" int hlb_set_state(hlb_solver* h, const void* f, int32_t where, int64_t t) {
+  if (!h || !f) return hlb_fail(HLB_ERR_ARG, "null argument");
+  if (t < 0) return hlb_fail(HLB_ERR_ARG, "negative time");
+  CUDA_TRY(cudaMemcpyAsync(h->f[0], f, h->state_bytes(),
+                           where == HLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+  if (where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->cur = 0;
+  h->phase = 0;
+  h->t = t;
+  return HLB_OK;
+}

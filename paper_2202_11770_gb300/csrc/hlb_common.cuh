@@ -1,0 +1,236 @@
+// hlb_common.cuh — device-side building blocks of the D3Q19 sparse-lattice
+// solver: velocity tables, shifted-population storage traits, link records,
+// kernel parameters, and the per-site gather (streaming + boundaries) and
+// BGK collision shared by the forward, readback and adjoint kernels.
+//
+// Method (arXiv 2202.11770): Section 2.2 (D3Q19, Eqs. 3a-3b, 4-6),
+// Section 2.3 (bounce-back walls, Ladd velocity iolets, ghost-density
+// pressure iolets), Section 3.2.3 (structure-of-arrays populations).
+// Streaming is done as a pull (gather) through the streaming-index table,
+// the ordering the paper's future-work list (Section 7, item 3) expects to
+// be faster than its push kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hlb {
+
+constexpr int Q = 19;
+
+// Velocity set (Section 2.2) in the order documented in hemegb.h.
+__host__ __device__ constexpr int cx(int i) {
+  constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+  return t[i];
+}
+__host__ __device__ constexpr int cy(int i) {
+  constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+  return t[i];
+}
+__host__ __device__ constexpr int cz(int i) {
+  constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+  return t[i];
+}
+// Opposite pairs are adjacent: 1<->2, 3<->4, ..., 17<->18.
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// Weights 1/3, 1/18, 1/36 (Section 2.2).
+template <typename R>
+__host__ __device__ constexpr R wgt(int i) {
+  return i == 0 ? R(1) / R(3) : (i <= 6 ? R(1) / R(18) : R(1) / R(36));
+}
+
+// ---------------------------------------------------------------------------
+// Storage traits: populations are stored shifted, h = f - w.
+// ---------------------------------------------------------------------------
+template <typename S> struct Real { using type = float; };
+template <> struct Real<double> { using type = double; };
+
+__device__ __forceinline__ float to_real(float v) { return v; }
+__device__ __forceinline__ double to_real(double v) { return v; }
+__device__ __forceinline__ float to_real(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_real(__half v) { return __half2float(v); }
+
+template <typename S> __device__ __forceinline__ S from_real(float v);
+template <> __device__ __forceinline__ float from_real<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_real<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half from_real<__half>(float v) { return __float2half_rn(v); }
+template <typename S> __device__ __forceinline__ S from_real(double v);
+template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
+
+// Cached load of a population (read-only for the whole kernel).
+template <typename S>
+__device__ __forceinline__ typename Real<S>::type ldpop(const S* p) {
+  return to_real(__ldg(p));
+}
+// Streaming load of the index table (read once per step, evict first).
+__device__ __forceinline__ int32_t ldidx(const int32_t* p) { return __ldcs(p); }
+// Streaming store of a population (next read is a full sweep later).
+template <typename S>
+__device__ __forceinline__ void stpop(S* p, typename Real<S>::type v) {
+  __stcs(p, from_real<S>(v));
+}
+
+// ---------------------------------------------------------------------------
+// Boundary links and per-launch parameters.
+// ---------------------------------------------------------------------------
+// One record per (site, pull direction) whose source crosses an iolet.  In
+// the device index table such a link carries the code -(2 + record index).
+struct LinkRec {
+  int32_t site;
+  int8_t dir;      // pull direction j: the source x - c_j is beyond the iolet
+  int8_t kind;     // 0 velocity, 1 pressure
+  int16_t iolet;
+  int32_t group;   // global amplitude group (velocity), -1 otherwise
+  float coef;      // velocity: 6 w_j W(x_m) (c_j . n); pressure: unused
+};
+static_assert(sizeof(LinkRec) == 16, "LinkRec is 16 bytes");
+
+constexpr int MAX_IOLETS = 128;
+
+struct IoletParam {
+  float nx, ny, nz;
+  float val;  // velocity iolet: waveform factor w(t); pressure iolet: rho(t) - 1
+};
+
+struct StepParams {
+  int64_t n;
+  float omega;          // 1 / tau
+  int32_t n_iolets;
+  int32_t ladd_rho_one;
+  int32_t ghost_full_u;
+  IoletParam io[MAX_IOLETS];
+};
+
+// ---------------------------------------------------------------------------
+// Moments and equilibrium in shifted form.
+//   rho = 1 + drho, drho = sum h_i;  j = sum h_i c_i;  u = j / rho
+//   f^eq_i - w_i = w_i (drho + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u))
+// which is Eq. 4 with the factors 1/2 (cs2 = 1/3).
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Macro {
+  R drho, rho, ux, uy, uz;
+};
+
+template <typename R>
+__device__ __forceinline__ Macro<R> moments(const R* h) {
+  R d = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    d += h[i];
+    if (cx(i)) jx += cx(i) > 0 ? h[i] : -h[i];
+    if (cy(i)) jy += cy(i) > 0 ? h[i] : -h[i];
+    if (cz(i)) jz += cz(i) > 0 ? h[i] : -h[i];
+  }
+  Macro<R> m;
+  m.drho = d;
+  m.rho = R(1) + d;
+  R inv = R(1) / m.rho;
+  m.ux = jx * inv;
+  m.uy = jy * inv;
+  m.uz = jz * inv;
+  return m;
+}
+
+template <typename R>
+__device__ __forceinline__ R cdotu(int i, R ux, R uy, R uz) {
+  R s = R(0);
+  if (cx(i)) s += cx(i) > 0 ? ux : -ux;
+  if (cy(i)) s += cy(i) > 0 ? uy : -uy;
+  if (cz(i)) s += cz(i) > 0 ? uz : -uz;
+  return s;
+}
+
+// Shifted equilibrium of direction i at (drho, rho, u).
+template <typename R>
+__device__ __forceinline__ R heq(int i, R drho, R rho, R ux, R uy, R uz, R usq15) {
+  R cu = cdotu<R>(i, ux, uy, uz);
+  return wgt<R>(i) * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
+}
+
+// BGK collision in place: h <- h + omega (heq - h)   (Eq. 3a, dt = 1).
+template <typename R>
+__device__ __forceinline__ void collide(R* h, R omega) {
+  Macro<R> m = moments<R>(h);
+  R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) h[i] += omega * (heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15) - h[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Gather of the pre-collision state f(t) at site x from the post-collision
+// state s'(t-1) (pull streaming, Eq. 3b) with boundaries:
+//   fluid source:   h_i = s'_i(x - c_i)
+//   wall link:      h_i = s'_ibar(x)                         (bounce-back)
+//   velocity iolet: h_i = s'_ibar(x) + coef rho_s A          (Ladd)
+//   pressure iolet: h_i = f^eq_i(rho_k, u_g) - w_i           (ghost density)
+// rho_s, u_s are the moments of s'(t-1) at x: BGK conserves mass and
+// momentum, so they equal the pre-collision moments at time t-1 that the
+// paper's push formulation uses for these boundaries.
+// Returns whether the site has an iolet link.
+// ---------------------------------------------------------------------------
+template <typename S>
+__device__ __forceinline__ bool gather_site(const S* __restrict__ fin, const int32_t* __restrict__ src,
+                                            int64_t n, int64_t x, typename Real<S>::type* h) {
+  h[0] = ldpop(fin + x);
+  bool any_iolet = false;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    int32_t s = ldidx(src + (int64_t)(i - 1) * n + x);
+    int64_t a = s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x;
+    h[i] = ldpop(fin + a);
+    any_iolet |= s <= -2;
+  }
+  return any_iolet;
+}
+
+// Boundary values of iolet links at site x (rare: only iolet sites).  On
+// entry h[i] of an iolet link already holds s'_ibar(x) (the gather selects
+// the own opposite slot for every non-fluid source).
+template <typename S>
+__device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int32_t* __restrict__ src,
+                                            const LinkRec* __restrict__ links, const float* __restrict__ amp,
+                                            const StepParams& p, int64_t x, typename Real<S>::type* h) {
+  using R = typename Real<S>::type;
+  const int64_t n = p.n;
+  // moments of the site's own post-collision state s'(t-1)
+  R d = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    R v = ldpop(fin + (int64_t)i * n + x);
+    d += v;
+    if (cx(i)) jx += cx(i) > 0 ? v : -v;
+    if (cy(i)) jy += cy(i) > 0 ? v : -v;
+    if (cz(i)) jz += cz(i) > 0 ? v : -v;
+  }
+  const R rho_s = R(1) + d;
+  const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    int32_t s = src[(int64_t)(i - 1) * n + x];
+    if (s > -2) continue;
+    const LinkRec L = links[-s - 2];
+    const IoletParam io = p.io[L.iolet];
+    if (L.kind == 0) {
+      R rho = p.ladd_rho_one ? R(1) : rho_s;
+      h[i] += R(L.coef) * rho * R(amp[L.group]) * R(io.val);
+    } else {
+      R gx = ux, gy = uy, gz = uz;
+      if (!p.ghost_full_u) {
+        R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
+        gx = un * R(io.nx);
+        gy = un * R(io.ny);
+        gz = un * R(io.nz);
+      }
+      R drho = R(io.val);
+      R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
+      h[i] = heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
+    }
+  }
+}
+
+}  // namespace hlb

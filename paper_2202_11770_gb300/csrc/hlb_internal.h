@@ -1,0 +1,83 @@
+// hlb_internal.h — host-side solver object and kernel launchers shared by
+// the translation units of libhemegb.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hemegb.h"
+#include "hlb_common.cuh"
+
+struct HostWave {
+  int32_t kind = HLB_WAVE_CONST;
+  double mean = 0, rel = 0, period = 1, phase = 0;
+  std::vector<double> samples;
+  double at(double t) const;
+};
+
+struct hlb_solver {
+  // lattice
+  int64_t n = 0;
+  int32_t n_iolets = 0;
+  std::vector<hlb_iolet> iolets;
+  std::vector<int32_t> group_offset;  // per iolet: first global amplitude group (-1: pressure)
+  int32_t n_groups_total = 0;
+  std::vector<int64_t> link_begin;    // per iolet: first link record (records sorted by iolet, group)
+  int64_t n_links = 0;
+  bool has_normals = false;
+
+  // options
+  int32_t precision = HLB_FP32;
+  int32_t scheme = HLB_PULL_AB;
+  int32_t ladd_rho_one = 0;
+  int32_t ghost_full_u = 0;
+
+  // state
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* f[2] = {nullptr, nullptr};    // population buffers [19][n] (storage precision)
+  int cur = 0;                        // buffer holding the current state
+  int phase = 0;                      // 0: buffer holds f(t) (pre-collision); 1: holds s'(t-1)
+  int64_t t = 0;
+  double tau = 1.0;
+  std::vector<HostWave> wave;         // per iolet
+  std::vector<double> amp;            // per global group
+
+  // device tables (inside the caller's workspace)
+  int32_t* d_src = nullptr;           // [18][n], iolet links re-coded to -(2 + record)
+  hlb::LinkRec* d_links = nullptr;
+  float* d_amp = nullptr;             // [n_groups_total]
+  float* d_normal = nullptr;          // [3][n] or null
+  float* d_stage = nullptr;           // [5][n] staging for host readback
+  double* d_red = nullptr;            // reduction scratch
+  int64_t red_slots = 0;
+
+  size_t elem_bytes() const;
+  size_t state_bytes() const { return elem_bytes() * 19 * (size_t)n; }
+  // kernel parameters for a launch that gathers with boundary data at time tb
+  hlb::StepParams params(int64_t tb) const;
+};
+
+// thread-local error text
+int hlb_fail(int code, const std::string& msg);
+int hlb_cuda_fail(cudaError_t e, const char* where);
+
+// ---- launchers (hlb_forward.cu) ----
+// One time step from the current state (fin) into fout.
+cudaError_t hlb_launch_step(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
+                            cudaStream_t s);
+// rho, u [3][n], wss of the current state, device outputs (any may be null).
+cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, bool gather, int64_t tb, float* rho,
+                              float* u, float* wss, cudaStream_t s);
+// Shifted pre-collision state into out [19][n] (storage precision).
+cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, bool gather, int64_t tb, void* out,
+                             cudaStream_t s);
+// Equilibrium initialisation; u0 [3][n] device or null.
+cudaError_t hlb_launch_init(const hlb_solver* h, void* f, double rho0, const float* u0, cudaStream_t s);
+// Mass partial sums into d_red[0..nb), then the final sums; flux per iolet.
+cudaError_t hlb_launch_reduce(const hlb_solver* h, const void* fin, bool gather, int64_t tb, double* out_dev,
+                              cudaStream_t s);
+int64_t hlb_reduce_slots(int64_t n, int32_t n_iolets);

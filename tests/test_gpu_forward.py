@@ -1,0 +1,277 @@
+"""GPU forward path vs the FP64 oracle, through the C ABI.
+
+Tolerances: FP32 storage and arithmetic must reach relative L2 velocity
+error <= 1e-5 after 1000 steps on the 12,352-site pipe; FP64 agrees to
+rounding (1e-11); integer-like behaviour (rest state, permutations) is exact.
+Sizes span many 256-site tiles with ragged tails; the full-size case runs the
+seeded 20M-site tree in the benchmark's launch configuration and checks one
+step against the oracle at every site.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_11770_gb300 import geometry as geo
+from helpers import hand_lattice
+
+pytestmark = pytest.mark.gpu
+
+hemegb = pytest.importorskip("paper_2202_11770_gb300.hemegb")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _both(lat, tau, setup, precision="fp32", **kw):
+    s = hemegb.Solver(lat, tau=tau, precision=precision, **kw)
+    o = oracle.Oracle(lat, tau=tau, ladd_rho_one=kw.get("ladd_rho_one", False),
+                      ghost_full_u=kw.get("ghost_full_u", False))
+    setup(s)
+    setup(o)
+    s.init_equilibrium()
+    o.init_equilibrium()
+    return s, o
+
+
+def _pipe_bc(x):
+    x.set_velocity(0, [1.0], 0.01)
+    x.set_pressure(1, 1.0)
+
+
+@pytest.fixture(scope="module")
+def pipe():
+    return geo.pipe(8.0, 64)
+
+
+def test_pipe_fp32_1000_steps(pipe):
+    s, o = _both(pipe, 0.8, _pipe_bc)
+    s.step(1000)
+    o.step(1000)
+    rho, u, wss = s.macros()
+    rho_o, u_o, wss_o = o.macros(pipe.wall_normal)
+    err_u = rel_l2(u, u_o)
+    assert err_u <= 1e-5, err_u
+    assert np.abs(rho - rho_o).max() < 1e-6
+    wall = ~np.isnan(wss_o)
+    assert np.array_equal(np.isnan(wss), ~wall)
+    assert rel_l2(wss[wall], wss_o[wall]) < 1e-4
+    mass, flux = s.reduce()
+    assert abs(mass - o.mass()) < 1e-9 * mass
+    assert np.allclose(flux, o.flux(), rtol=1e-4, atol=1e-9)
+
+
+def test_pipe_fp64_matches_to_rounding(pipe):
+    def bc(x):
+        x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.01, "rel": 0.5, "period": 60.0})
+        x.set_pressure(1, {"kind": "cosine", "mean": 1.0, "rel": 0.001, "period": 45.0})
+    s, o = _both(pipe, 0.7, bc, precision="fp64")
+    s.step(300)
+    o.step(300)
+    f, t = s.state()
+    assert t == 300
+    from conftest import load_d3q19
+    _, w = load_d3q19()
+    f_o = o.state().T - w[:, None]
+    assert np.abs(f - f_o).max() < 1e-13
+    rho, u, wss = s.macros()
+    _, u_o, _ = o.macros(pipe.wall_normal)
+    assert rel_l2(u, u_o) < 1e-7          # macros are returned as float32
+    mass, flux = s.reduce()
+    assert abs(mass - o.mass()) < 1e-12 * mass
+    assert np.allclose(flux, o.flux(), rtol=1e-9, atol=1e-13)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16", "fp64"])
+def test_rest_state_exact(pipe, prec):
+    def bc(x):
+        x.set_velocity(0, [1.0], 0.0)
+        x.set_pressure(1, 1.0)
+    s = hemegb.Solver(pipe, tau=0.8, precision=prec)
+    bc(s)
+    s.init_equilibrium()
+    s.step(1000)
+    f, _ = s.state()
+    assert not f.view(np.uint8).any()         # shifted state stays exactly zero
+
+
+def test_streaming_permutation_bruteforce(d3q19):
+    c, w = d3q19
+    from helpers import opposite_table
+    opp = opposite_table(c)
+    rng = np.random.default_rng(3)
+    pts = [(x, y, z) for x in range(9) for y in range(7) for z in range(6) if (x * 7 + y * 3 + z) % 5]
+    lat = hand_lattice(pts, c)
+    assert lat.n > 256 and lat.n % 256   # several tiles, ragged tail
+    n = lat.n
+    rho0 = rng.uniform(0.9, 1.1, n)
+    u0 = rng.uniform(-0.05, 0.05, (n, 3))
+    f0 = np.stack([oracle.feq(rho0[k], u0[k]) for k in range(n)])     # equilibrium: collision is identity
+    s = hemegb.Solver(lat, tau=0.7, precision="fp64")
+    s.set_state((f0 - w).T.copy(), 0)
+    s.step(2)
+    got, _ = s.state()
+    index = {tuple(p): k for k, p in enumerate(lat.xyz.tolist())}
+    exp = f0.copy()
+    for _ in range(2):
+        nxt = np.full_like(exp, np.nan)
+        for k, p in enumerate(lat.xyz):
+            for i in range(19):
+                q = tuple((p + c[i]).tolist())
+                if q in index:
+                    nxt[index[q], i] = exp[k, i]
+                else:
+                    nxt[k, opp[i]] = exp[k, i]
+        exp = nxt
+    assert np.abs(got.T + w - exp).max() < 1e-14
+
+
+def test_isolated_site_and_small_lattices(d3q19):
+    c, _ = d3q19
+    for pts in ([(0, 0, 0)], [(0, 0, 0), (1, 0, 0)], [(0, 0, 0), (1, 1, 0), (1, 1, 1)]):
+        lat = hand_lattice(pts, c)
+        s = hemegb.Solver(lat, tau=0.6, precision="fp32")
+        o = oracle.Oracle(lat, tau=0.6)
+        rng = np.random.default_rng(len(pts))
+        u0 = rng.uniform(-0.05, 0.05, (lat.n, 3))
+        s.init_equilibrium(1.0, u0.T.astype(np.float32).copy())
+        o.init_equilibrium(1.0, u0.astype(np.float32).astype(np.float64))
+        s.step(7)
+        o.step(7)
+        rho, u, _ = s.macros()
+        rho_o, u_o, _ = o.macros()
+        assert np.abs(u - u_o).max() < 1e-7
+        assert np.abs(rho - rho_o).max() < 1e-6
+
+
+def test_tree_several_tiles_fp32():
+    lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0)
+    assert lat.n % 256
+
+    def bc(x):
+        x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 200.0})
+        for k in range(1, len(lat.iolets)):
+            x.set_pressure(k, 1.0)
+    s, o = _both(lat, 0.55, bc)
+    s.step(300)
+    o.step(300)
+    _, u, wss = s.macros()
+    _, u_o, wss_o = o.macros(lat.wall_normal)
+    assert rel_l2(u, u_o) <= 1e-5
+    wall = ~np.isnan(wss_o)
+    assert rel_l2(wss[wall], wss_o[wall]) < 1e-4
+
+
+@pytest.mark.parametrize("opts", [dict(ladd_rho_one=True), dict(ghost_full_u=True)])
+def test_boundary_options(opts):
+    lat = geo.tree(1, 5, root_radius=5.0, length_ratio=5.0)
+
+    def bc(x):
+        x.set_velocity(0, [1.0], 0.02)
+        for k in range(1, len(lat.iolets)):
+            x.set_pressure(k, 1.0 - 0.001 * k)
+    s, o = _both(lat, 0.6, bc, precision="fp64", **opts)
+    s.step(100)
+    o.step(100)
+    _, u, _ = s.macros()
+    _, u_o, _ = o.macros()
+    assert rel_l2(u, u_o) < 1e-7
+
+
+def test_mass_budget_and_closed_conservation():
+    lat = geo.pipe(5.0, 20, geo.WALL, geo.WALL)
+    s = hemegb.Solver(lat, tau=0.6, precision="fp64")
+    rng = np.random.default_rng(5)
+    s.init_equilibrium(1.0, rng.uniform(-0.02, 0.02, (3, lat.n)).astype(np.float32))
+    m0, _ = s.reduce()
+    s.step(500)
+    m1, _ = s.reduce()
+    assert abs(m1 - m0) < 1e-13 * m0
+
+    lat = geo.pipe(6.0, 24)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 1e-12)):
+        s = hemegb.Solver(lat, tau=0.7, precision=prec)
+        s.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 40.0})
+        s.set_pressure(1, {"kind": "cosine", "mean": 1.0, "rel": 0.002, "period": 25.0})
+        s.init_equilibrium()
+        m, _ = s.reduce()
+        for _ in range(30):
+            s.step(1)
+            m1, fl = s.reduce()
+            # the FP64 reduction sees exactly the stored values: the budget is exact to FP64 rounding
+            assert abs((m1 - m) - fl.sum()) < tol * m1 + (2e-6 if prec == "fp32" else 0)
+            m = m1
+
+
+def test_state_roundtrip_resumes_bit_identical(pipe):
+    s, _ = _both(pipe, 0.8, _pipe_bc)
+    s.step(37)
+    f, t = s.state()
+    s.step(20)
+    ref, _ = s.state()
+    s2 = hemegb.Solver(pipe, tau=0.8, precision="fp32")
+    _pipe_bc(s2)
+    s2.set_state(f, t)
+    s2.step(20)
+    got, t2 = s2.state()
+    assert t2 == t + 20
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("prec,bound", [("bf16", 0.1), ("fp16", 0.02)])
+def test_16bit_storage_error_reported(pipe, prec, bound):
+    s, o = _both(pipe, 0.8, _pipe_bc, precision=prec)
+    s.step(1000)
+    o.step(1000)
+    _, u, _ = s.macros()
+    _, u_o, _ = o.macros(pipe.wall_normal)
+    err = rel_l2(u, u_o)
+    print(f"{prec}: rel L2(u) after 1000 steps = {err:.3e}")
+    assert err < bound
+
+
+def test_invalid_arguments(pipe):
+    s = hemegb.Solver(pipe, tau=0.8)
+    with pytest.raises(hemegb.HlbError):
+        s.set_tau(0.5)
+    with pytest.raises(hemegb.HlbError):
+        s.set_pressure(0, 1.0)              # iolet 0 is a velocity iolet
+    with pytest.raises(hemegb.HlbError):
+        s.set_velocity(0, [1.0, 2.0], 0.01)  # one group only
+    with pytest.raises(hemegb.HlbError):
+        s.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.01, "rel": 0.5, "period": 0.0})
+    s.step(0)
+    assert s.t == 0
+
+
+def test_full_size_tree_one_step_vs_oracle(d3q19):
+    """Seeded 20M-site depth-6 tree (the benchmark workload), FP32 solver in
+    the benchmark's launch configuration: after 5 pulsatile steps, one more
+    step is compared with the oracle's step from the same state, at every
+    site; mass budget checked at full size."""
+    _, w = d3q19
+    lat = geo.tree(6, 2202, target_sites=20_000_000, length_ratio=5.0)
+    assert abs(lat.n - 20_000_000) < 0.02 * 20_000_000
+    s = hemegb.Solver(lat, tau=0.55, precision="fp32")
+    s.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 2000.0})
+    for k in range(1, len(lat.iolets)):
+        s.set_pressure(k, 1.0)
+    s.init_equilibrium()
+    s.step(5)
+    m5, _ = s.reduce()
+    f5, t5 = s.state()
+    s.step(1)
+    m6, fl6 = s.reduce()
+    assert abs((m6 - m5) - fl6.sum()) < 1e-9 * m6
+    f6, _ = s.state()
+
+    o = oracle.Oracle(lat, tau=0.55)
+    o.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 2000.0})
+    for k in range(1, len(lat.iolets)):
+        o.set_pressure(k, 1.0)
+    o.set_state((f5.astype(np.float64) + w[:, None]).T, t5)
+    o.step(1)
+    f6o = o.state()
+    diff = np.abs(f6.T.astype(np.float64) + w[None, :] - f6o)
+    assert diff.max() < 2e-8
+    assert abs(o.mass() - m6) < 1e-9 * m6
