@@ -121,14 +121,13 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 def tree_lattice(target):
-    from paper_2202_11770_gb300 import geometry
-    return geometry.tree(6, 2202, target_sites=target, length_ratio=5.0)
+    from paper_2202_11770_gb300 import workloads
+    return workloads.tree_lattice(target)
 
 
 def set_bc(x, lat):
-    x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 2000.0})
-    for k in range(1, len(lat.iolets)):
-        x.set_pressure(k, 1.0)
+    from paper_2202_11770_gb300 import workloads
+    workloads.apply_tree_bc(x, lat)
 
 
 def time_form(lat, precision, steps, warmup, torch, dist=None):
@@ -188,6 +187,44 @@ def e2e_job(lat, steps, torch):
     del s
     torch.cuda.empty_cache()
     return n * steps / dt / 1e6, h2d_step, d2h_step
+
+
+def adjoint_ratio(steps, torch):
+    """Adjoint (forward with sqrt(N) checkpoints + recompute + reverse) vs
+    forward-only time over the same N steps: seeded depth-4 tree, ~2M sites,
+    64 inlet amplitude groups, FP32."""
+    from paper_2202_11770_gb300 import hemegb, workloads
+    lat, obj = workloads.adjoint_case()
+    s = hemegb.Solver(lat, tau=0.55, precision="fp32")
+    workloads.apply_tree_bc(s, lat)
+    ws = s.adjoint_workspace(steps, obj.sites.size)
+    s.init_equilibrium()
+    s.step(10)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.init_equilibrium()
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1)
+    s.init_equilibrium()
+    s.adjoint(min(steps, 50), obj.sites, obj.target, obj.axis, workspace=ws)   # warm-up
+    s.init_equilibrium()
+    torch.cuda.synchronize()
+    e0.record(s.stream)
+    J, dtau, damp = s.adjoint(steps, obj.sites, obj.target, obj.axis, workspace=ws)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    adj = e0.elapsed_time(e1)
+    K = int(math.ceil(math.sqrt(steps)))
+    out = {"workload": "seeded depth-4 tree, 64 inlet amplitude groups, FP32", "n_sites": lat.n, "steps": steps,
+           "checkpoint_interval": K, "forward_ms": fwd, "adjoint_ms": adj, "ratio": adj / fwd,
+           "J": J, "dJ_dtau": dtau, "probe_sites": int(obj.sites.size),
+           "adjoint_workspace_gb": ws[2] / 1e9}
+    del s, ws
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(lat, steps):
@@ -277,6 +314,10 @@ def run_ours(args):
                          "gbs": achieved, "frac_of_measured_peak": achieved / peak,
                          "bytes_per_site": bytes_per_site(4)}
 
+    adjoint = None
+    if not args.quick and args.adjoint_steps > 0:
+        adjoint = adjoint_ratio(args.adjoint_steps, torch)
+
     e2e = None
     if not args.quick:
         v, h2d, d2h = e2e_job(lat, args.e2e_steps, torch)
@@ -305,6 +346,7 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": args.steps,
             "forms": forms,
+            "adjoint": adjoint,
         }
         print(json.dumps(line))
     if dist is not None:
@@ -321,6 +363,7 @@ def main():
     ap.add_argument("--sites", type=int, default=20_000_000)
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--ref-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="FP32 only, no e2e (profiling runs)")

@@ -87,16 +87,16 @@ StepParams hlb_solver::params(int64_t tb) const {
   StepParams p;
   memset(&p, 0, sizeof p);
   p.n = n;
-  p.omega = (float)(1.0 / tau);
+  p.omega = 1.0 / tau;
   p.n_iolets = n_iolets;
   p.ladd_rho_one = ladd_rho_one;
   p.ghost_full_u = ghost_full_u;
   for (int k = 0; k < n_iolets; ++k) {
-    p.io[k].nx = (float)iolets[k].normal[0];
-    p.io[k].ny = (float)iolets[k].normal[1];
-    p.io[k].nz = (float)iolets[k].normal[2];
+    p.io[k].nx = iolets[k].normal[0];
+    p.io[k].ny = iolets[k].normal[1];
+    p.io[k].nz = iolets[k].normal[2];
     double w = wave[k].at((double)tb);
-    p.io[k].val = (float)(iolets[k].kind == HLB_VELOCITY ? w : w - 1.0);
+    p.io[k].val = iolets[k].kind == HLB_VELOCITY ? w : w - 1.0;
   }
   return p;
 }
@@ -167,7 +167,7 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.f1 = off; off += state;
   y.src = off; off += align_up(sizeof(int32_t) * 18 * (size_t)n);
   y.links = off; off += align_up(sizeof(LinkRec) * (size_t)std::max<int64_t>(y.n_links, 1));
-  y.amp = off; off += align_up(sizeof(float) * (size_t)std::max(y.n_groups, 1));
+  y.amp = off; off += align_up(sizeof(double) * (size_t)std::max(y.n_groups, 1));
   y.normal = off; off += L->wall_normal ? align_up(sizeof(float) * 3 * (size_t)n) : 0;
   y.stage = off; off += align_up(sizeof(float) * 5 * (size_t)n);
   y.red = off; off += align_up(sizeof(double) * (size_t)hlb_reduce_slots(n, L->n_iolets));
@@ -237,7 +237,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->f[1] = base + y.f1;
   h->d_src = (int32_t*)(base + y.src);
   h->d_links = (LinkRec*)(base + y.links);
-  h->d_amp = (float*)(base + y.amp);
+  h->d_amp = (double*)(base + y.amp);
   h->d_normal = L->wall_normal ? (float*)(base + y.normal) : nullptr;
   h->d_stage = (float*)(base + y.stage);
   h->d_red = (double*)(base + y.red);
@@ -260,6 +260,14 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->n_links = y.n_links;
   h->link_begin.resize(h->n_iolets + 1);
   for (int k = 0; k <= h->n_iolets; ++k) h->link_begin[k] = count[bucket_base[k]];
+  h->group_link_begin.assign(g + 1, 0);
+  for (int k = 0; k < h->n_iolets; ++k) {
+    if (h->iolets[k].kind != HLB_VELOCITY) continue;
+    for (int gl = 0; gl < h->iolets[k].n_groups; ++gl) {
+      h->group_link_begin[h->group_offset[k] + gl] = count[bucket_base[k] + gl];
+      h->group_link_begin[h->group_offset[k] + gl + 1] = count[bucket_base[k] + gl + 1];
+    }
+  }
   std::vector<LinkRec> recs((size_t)std::max<int64_t>(y.n_links, 1));
   std::vector<int32_t> src(L->src, L->src + (size_t)18 * n);
   std::vector<int64_t> fillpos(count.begin(), count.end() - 1);
@@ -277,7 +285,8 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
       R.kind = (int8_t)io.kind;
       R.iolet = (int16_t)k;
       R.group = io.kind == HLB_VELOCITY ? h->group_offset[k] + gl : -1;
-      R.coef = 0.f;
+      R.pad = 0;
+      R.coef = 0.0;
       if (io.kind == HLB_VELOCITY) {
         // Ladd weight at the link midpoint x - c_j / 2
         double m[3] = {L->xyz[3 * x] - 0.5 * cx(j), L->xyz[3 * x + 1] - 0.5 * cy(j), L->xyz[3 * x + 2] - 0.5 * cz(j)};
@@ -291,7 +300,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
         double W = std::max(0.0, 1.0 - r2 / (io.radius * io.radius));
         double cn = cx(j) * io.normal[0] + cy(j) * io.normal[1] + cz(j) * io.normal[2];
         // f_j(x) = f'_jbar(x) - 2 w rho (c_jbar . u_w) / cs2 = f'_jbar(x) + 6 w_j rho A W (c_j . n)
-        R.coef = (float)(6.0 * wgt<double>(j) * W * cn);
+        R.coef = 6.0 * wgt<double>(j) * W * cn;
       }
       src[(size_t)(j - 1) * n + x] = -(int32_t)(2 + r);
     }
@@ -299,12 +308,12 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   cudaStream_t st = h->stream;
   int64_t nb = (n + 255) / 256;
   std::vector<int64_t> begin(h->link_begin);
-  std::vector<float> ampf(std::max(g, 1), 0.f);
+  std::vector<double> ampf(std::max(g, 1), 0.0);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * 18 * (size_t)n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && y.n_links > 0)
     e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(float) * ampf.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(double) * ampf.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && h->d_normal)
     e = cudaMemcpyAsync(h->d_normal, L->wall_normal, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -355,12 +364,8 @@ extern "C" int hlb_set_velocity_waveform(hlb_solver* h, int32_t k, const double*
   for (int gi = 0; gi < n_groups; ++gi)
     if (!std::isfinite(amp[gi])) return hlb_fail(HLB_ERR_ARG, "non-finite amplitude");
   h->wave[k] = hw;
-  std::vector<float> af(n_groups);
-  for (int gi = 0; gi < n_groups; ++gi) {
-    h->amp[h->group_offset[k] + gi] = amp[gi];
-    af[gi] = (float)amp[gi];
-  }
-  CUDA_TRY(cudaMemcpyAsync(h->d_amp + h->group_offset[k], af.data(), sizeof(float) * n_groups,
+  for (int gi = 0; gi < n_groups; ++gi) h->amp[h->group_offset[k] + gi] = amp[gi];
+  CUDA_TRY(cudaMemcpyAsync(h->d_amp + h->group_offset[k], amp, sizeof(double) * n_groups,
                            cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return HLB_OK;

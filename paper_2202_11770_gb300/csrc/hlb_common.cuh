@@ -85,23 +85,27 @@ struct LinkRec {
   int8_t kind;     // 0 velocity, 1 pressure
   int16_t iolet;
   int32_t group;   // global amplitude group (velocity), -1 otherwise
-  float coef;      // velocity: 6 w_j W(x_m) (c_j . n); pressure: unused
+  int32_t pad;
+  double coef;     // velocity: 6 w_j W(x_m) (c_j . n); pressure: unused
 };
-static_assert(sizeof(LinkRec) == 16, "LinkRec is 16 bytes");
+static_assert(sizeof(LinkRec) == 24, "LinkRec is 24 bytes");
 
 constexpr int MAX_IOLETS = 128;
 
+// Parameters are carried in double and rounded to the compute type at use,
+// so that FP64 storage sees no FP32-rounded coefficient anywhere.
 struct IoletParam {
-  float nx, ny, nz;
-  float val;  // velocity iolet: waveform factor w(t); pressure iolet: rho(t) - 1
+  double nx, ny, nz;
+  double val;  // velocity iolet: waveform factor w(t); pressure iolet: rho(t) - 1
 };
 
 struct StepParams {
   int64_t n;
-  float omega;          // 1 / tau
+  double omega;         // 1 / tau
   int32_t n_iolets;
   int32_t ladd_rho_one;
   int32_t ghost_full_u;
+  int32_t pad;
   IoletParam io[MAX_IOLETS];
 };
 
@@ -193,7 +197,7 @@ __device__ __forceinline__ bool gather_site(const S* __restrict__ fin, const int
 // the own opposite slot for every non-fluid source).
 template <typename S>
 __device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int32_t* __restrict__ src,
-                                            const LinkRec* __restrict__ links, const float* __restrict__ amp,
+                                            const LinkRec* __restrict__ links, const double* __restrict__ amp,
                                             const StepParams& p, int64_t x, typename Real<S>::type* h) {
   using R = typename Real<S>::type;
   const int64_t n = p.n;

@@ -29,7 +29,7 @@ template <typename S, bool GATHER>
 __global__ void __launch_bounds__(BLOCK) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                                 const int32_t* __restrict__ src,
                                                 const LinkRec* __restrict__ links,
-                                                const float* __restrict__ amp, const StepParams p) {
+                                                const double* __restrict__ amp, const StepParams p) {
   using R = typename Real<S>::type;
   const int64_t n = p.n;
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(BLOCK) k_step(const S* __restrict__ fin, S* __
 
 template <typename S, bool GATHER>
 __device__ __forceinline__ void load_state(const S* __restrict__ fin, const int32_t* __restrict__ src,
-                                           const LinkRec* __restrict__ links, const float* __restrict__ amp,
+                                           const LinkRec* __restrict__ links, const double* __restrict__ amp,
                                            const StepParams& p, int64_t x, typename Real<S>::type* h) {
   if (GATHER) {
     if (gather_site<S>(fin, src, p.n, x, h)) iolet_fixup<S>(fin, src, links, amp, p, x, h);
@@ -64,7 +64,7 @@ __device__ __forceinline__ void load_state(const S* __restrict__ fin, const int3
 template <typename S, bool GATHER>
 __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                   const LinkRec* __restrict__ links,
-                                                  const float* __restrict__ amp,
+                                                  const double* __restrict__ amp,
                                                   const float* __restrict__ normal, const StepParams p,
                                                   float* __restrict__ rho_out, float* __restrict__ u_out,
                                                   float* __restrict__ wss_out) {
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, con
 template <typename S, bool GATHER>
 __global__ void __launch_bounds__(BLOCK) k_state(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                  const LinkRec* __restrict__ links,
-                                                 const float* __restrict__ amp, const StepParams p,
+                                                 const double* __restrict__ amp, const StepParams p,
                                                  S* __restrict__ out) {
   using R = typename Real<S>::type;
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
@@ -183,7 +183,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 template <typename S, bool GATHER>
 __global__ void __launch_bounds__(BLOCK) k_mass(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                 const LinkRec* __restrict__ links,
-                                                const float* __restrict__ amp, const StepParams p,
+                                                const double* __restrict__ amp, const StepParams p,
                                                 double* __restrict__ part) {
   using R = typename Real<S>::type;
   __shared__ double sh[BLOCK / 32];
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(BLOCK) k_mass(const S* __restrict__ fin, const
 template <typename S>
 __global__ void __launch_bounds__(BLOCK) k_flux(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                 const LinkRec* __restrict__ links,
-                                                const float* __restrict__ amp, const StepParams p,
+                                                const double* __restrict__ amp, const StepParams p,
                                                 const int64_t* __restrict__ begin, double* __restrict__ out) {
   using R = typename Real<S>::type;
   __shared__ double sh[BLOCK / 32];

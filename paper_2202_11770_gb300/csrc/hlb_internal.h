@@ -26,6 +26,7 @@ struct hlb_solver {
   std::vector<int32_t> group_offset;  // per iolet: first global amplitude group (-1: pressure)
   int32_t n_groups_total = 0;
   std::vector<int64_t> link_begin;    // per iolet: first link record (records sorted by iolet, group)
+  std::vector<int64_t> group_link_begin;  // per global amplitude group: first record; [G] = end of the last
   int64_t n_links = 0;
   bool has_normals = false;
 
@@ -49,7 +50,7 @@ struct hlb_solver {
   // device tables (inside the caller's workspace)
   int32_t* d_src = nullptr;           // [18][n], iolet links re-coded to -(2 + record)
   hlb::LinkRec* d_links = nullptr;
-  float* d_amp = nullptr;             // [n_groups_total]
+  double* d_amp = nullptr;            // [n_groups_total]
   float* d_normal = nullptr;          // [3][n] or null
   float* d_stage = nullptr;           // [5][n] staging for host readback
   double* d_red = nullptr;            // reduction scratch

@@ -159,6 +159,31 @@ def hlb_reduce(h, n_iolets):
     return mass.value, np.array(flux[:n_iolets], dtype=np.float64), rc
 
 
+def make_objective(sites, target, axis):
+    """(hlb_objective, keep-alive arrays) from probe sites, targets and axis."""
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    target = np.ascontiguousarray(target, dtype=np.float64)
+    obj = hlb_objective(n_probe=sites.size, sites=sites.ctypes.data_as(C.POINTER(C.c_int64)),
+                        target=target.ctypes.data_as(C.POINTER(C.c_double)),
+                        axis=tuple(float(a) for a in axis))
+    return obj, (sites, target)
+
+
+def hlb_adjoint_workspace_bytes(h, nsteps, n_probe) -> int:
+    nb = C.c_size_t()
+    _check(library().hlb_adjoint_workspace_bytes(h, int(nsteps), int(n_probe), C.byref(nb)))
+    return nb.value
+
+
+def hlb_adjoint_run(h, nsteps, obj, ws_ptr, ws_bytes, n_groups):
+    J = C.c_double()
+    dtau = C.c_double()
+    damp = (C.c_double * max(1, n_groups))()
+    _check(library().hlb_adjoint_run(h, int(nsteps), C.byref(obj), _P(ws_ptr), ws_bytes, C.byref(J),
+                                     C.byref(dtau), damp))
+    return J.value, dtau.value, np.array(damp[:n_groups])
+
+
 def make_waveform(w):
     """dict (or number) -> (hlb_waveform, keep-alive buffer).
 
@@ -318,25 +343,20 @@ class Solver:
         assert f.nbytes == 19 * self.n * _ELEM[self.precision]
         _check(self._lib.hlb_set_state(self._h, _P(f.ctypes.data), HLB_HOST, int(t)))
 
-    def adjoint(self, nsteps, sites, target, axis):
-        """(J, dJ/dtau, dJ/da[groups]) over nsteps from the current state."""
-        torch = self._torch
-        sites = np.ascontiguousarray(sites, dtype=np.int64)
-        target = np.ascontiguousarray(target, dtype=np.float64)
-        obj = hlb_objective(n_probe=sites.size, sites=sites.ctypes.data_as(C.POINTER(C.c_int64)),
-                            target=target.ctypes.data_as(C.POINTER(C.c_double)),
-                            axis=tuple(float(a) for a in axis))
-        nb = C.c_size_t()
-        _check(self._lib.hlb_adjoint_workspace_bytes(self._h, int(nsteps), sites.size, C.byref(nb)))
-        ws = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
-        ptr = (ws.data_ptr() + 255) & ~255
-        J = C.c_double()
-        dtau = C.c_double()
-        damp = (C.c_double * max(1, self.n_groups))()
-        _check(self._lib.hlb_adjoint_run(self._h, int(nsteps), C.byref(obj), _P(ptr), nb.value, C.byref(J),
-                                         C.byref(dtau), damp))
-        del ws
-        return J.value, dtau.value, np.array(damp[: self.n_groups])
+    def adjoint_workspace(self, nsteps, n_probe):
+        """A device workspace (uint8 tensor, 256-byte aligned pointer) for adjoint()."""
+        nb = hlb_adjoint_workspace_bytes(self._h, nsteps, n_probe)
+        ws = self._torch.empty(nb + 256, dtype=self._torch.uint8, device="cuda")
+        return ws, (ws.data_ptr() + 255) & ~255, nb
+
+    def adjoint(self, nsteps, sites, target, axis, workspace=None):
+        """(J, dJ/dtau, dJ/da[groups]) over nsteps from the current state.
+
+        ``workspace`` may be a tuple from adjoint_workspace(); otherwise one
+        is allocated for the call."""
+        obj, keep = make_objective(sites, target, axis)
+        ws = workspace if workspace is not None else self.adjoint_workspace(nsteps, obj.n_probe)
+        return hlb_adjoint_run(self._h, nsteps, obj, ws[1], ws[2], self.n_groups)
 
 
 def bf16_to_float(a: np.ndarray) -> np.ndarray:

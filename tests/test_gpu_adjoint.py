@@ -1,0 +1,104 @@
+"""GPU discrete adjoint vs the oracle's FP64 adjoint and central differences.
+
+* FP64 storage: the GPU adjoint (pull-form transpose, gathers) equals the
+  oracle's explicit-Jacobian push-form adjoint to rounding.
+* FP32 storage on a ~50k-site depth-2 tree: within 1e-4 relative of the
+  oracle's FP64 adjoint.
+* Full size (seeded depth-4 tree, ~2M sites, 64 inlet amplitude groups,
+  N = 2000 steps, sqrt(N) checkpoints): the FP32 adjoint agrees within 1e-3
+  with central differences (h = 1e-4) of the GPU FP64 forward on dJ/dtau,
+  four single amplitudes and four random amplitude directions.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_11770_gb300 import geometry as geo, workloads
+
+pytestmark = pytest.mark.gpu
+hemegb = pytest.importorskip("paper_2202_11770_gb300.hemegb")
+
+
+def _setup(x, lat, amps):
+    x.set_velocity(0, amps, {"kind": "cosine", "mean": 0.03, "rel": 0.5, "period": 50.0})
+    for k in range(1, len(lat.iolets)):
+        x.set_pressure(k, {"kind": "cosine", "mean": 1.0, "rel": 0.001 * k, "period": 30.0})
+    x.init_equilibrium()
+
+
+@pytest.mark.parametrize("opts", [(False, False), (True, True)])
+def test_fp64_adjoint_equals_oracle(opts):
+    lat = geo.tree(1, 7, root_radius=4.0, length_ratio=5.0, n_sectors=2, n_rings=2)
+    N, tau = 40, 0.7
+    probe = np.nonzero(lat.xyz[:, 2] == int(lat.info["root_length"] // 2))[0]
+    rng = np.random.default_rng(1)
+    target = 0.02 * (1 + 0.1 * rng.uniform(-1, 1, probe.size))
+    amps = np.array([1.0, 0.9, 1.1, 0.95])
+    o = oracle.Oracle(lat, tau, *opts)
+    _setup(o, lat, amps)
+    J_o, dtau_o, damp_o = o.adjoint(N, probe, target, [0, 0, 1])
+    s = hemegb.Solver(lat, tau=tau, precision="fp64", ladd_rho_one=opts[0], ghost_full_u=opts[1])
+    _setup(s, lat, amps)
+    J, dtau, damp = s.adjoint(N, probe, target, [0, 0, 1])
+    assert s.t == N
+    assert J == pytest.approx(J_o, rel=1e-12)
+    assert dtau == pytest.approx(dtau_o, rel=1e-9)
+    assert np.allclose(damp, damp_o, rtol=1e-9, atol=0)
+
+
+def test_fp32_adjoint_vs_oracle_depth2_tree():
+    lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0, n_sectors=8, n_rings=8)
+    obj = workloads.root_midplane_objective(lat, seed=2202)
+    N, tau = 100, 0.6
+    amps = 1.0 + 0.05 * np.random.default_rng(2).uniform(-1, 1, 64)
+    o = oracle.Oracle(lat, tau)
+    _setup(o, lat, amps)
+    J_o, dtau_o, damp_o = o.adjoint(N, obj.sites, obj.target, obj.axis)
+    s = hemegb.Solver(lat, tau=tau, precision="fp32")
+    _setup(s, lat, amps)
+    J, dtau, damp = s.adjoint(N, obj.sites, obj.target, obj.axis)
+    assert J == pytest.approx(J_o, rel=1e-4)
+    assert dtau == pytest.approx(dtau_o, rel=1e-4)
+    assert np.linalg.norm(damp - damp_o) <= 1e-4 * np.linalg.norm(damp_o)
+
+
+def test_adjoint_validation():
+    lat = geo.pipe(4.0, 8)
+    s = hemegb.Solver(lat, tau=0.7, precision="bf16")
+    with pytest.raises(hemegb.HlbError):
+        s.adjoint(10, [1, 2], [0.0, 0.0], [0, 0, 1])     # 16-bit storage has no adjoint
+    s = hemegb.Solver(lat, tau=0.7, precision="fp32")
+    with pytest.raises(hemegb.HlbError):
+        s.adjoint(10, [1, 1], [0.0, 0.0], [0, 0, 1])     # duplicate probes
+    with pytest.raises(hemegb.HlbError):
+        s.adjoint(10, [lat.n], [0.0], [0, 0, 1])         # out of range
+    with pytest.raises(hemegb.HlbError):
+        s.adjoint(0, [1], [0.0], [0, 0, 1])
+
+
+def test_full_size_adjoint_vs_central_differences():
+    lat, obj = workloads.adjoint_case()
+    assert abs(lat.n - 2_000_000) < 0.02 * 2_000_000
+    assert lat.iolets[0].n_groups == 64
+    N, tau, h = 2000, 0.55, 1e-4
+    amps = np.ones(64)
+
+    def run(precision, tau_, amps_):
+        s = hemegb.Solver(lat, tau=tau_, precision=precision)
+        workloads.apply_tree_bc(s, lat, amps=amps_)
+        s.init_equilibrium()
+        out = s.adjoint(N, obj.sites, obj.target, obj.axis)
+        del s
+        return out
+
+    J, dtau, damp = run("fp32", tau, amps)
+    assert damp.shape == (64,) and np.isfinite(damp).all()
+    Jp = run("fp64", tau + h, amps)[0]
+    Jm = run("fp64", tau - h, amps)[0]
+    fd = (Jp - Jm) / (2 * h)
+    assert abs(dtau - fd) <= 1e-3 * abs(fd), (dtau, fd)
+    rng = np.random.default_rng(11770)
+    dirs = [np.eye(64)[g] for g in (0, 21, 42, 63)] + [rng.normal(size=64) for _ in range(4)]
+    for d in dirs:
+        fd = (run("fp64", tau, amps + h * d)[0] - run("fp64", tau, amps - h * d)[0]) / (2 * h)
+        assert abs(damp @ d - fd) <= 1e-3 * abs(fd), (damp @ d, fd)
