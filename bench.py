@@ -40,18 +40,27 @@ sys.path.insert(0, str(ROOT))
 METRIC = "fluid-site MLUPS and HBM GB/s (% of peak), FP32 vs 16-bit store; adjoint/fwd"
 WORKLOAD = "seeded depth-6 vessel tree, 20M fluid sites, D3Q19 LBGK tau=0.55, pulsatile Ladd inlet, 64 pressure outlets"
 
-# Algorithmic bytes per site update of the pull A-B step: 19 populations read
-# + 19 written (storage precision) + the int32 streaming-index table
-# (18 x 4 B).  Boundary-link records are O(boundary sites) and not counted.
-def bytes_per_site(elem: int) -> int:
-    return 19 * elem * 2 + 18 * 4
+# Algorithmic bytes per site update (storage element size e): 19 populations
+# read + 19 written, plus the int32 streaming-index table (18 x 4 B) when the
+# kernel gathers through it.  Pull A-B gathers every step; the AA pattern
+# only on odd steps.  Boundary-link records are O(boundary sites), not counted.
+def bytes_per_site(elem: int, kernel: str = "ab") -> float:
+    local = 19 * elem * 2
+    if kernel in ("ab", "aa_odd"):
+        return local + 18 * 4
+    if kernel == "aa_even":
+        return local
+    if kernel == "aa":
+        return local + 18 * 4 / 2
+    raise ValueError(kernel)
 
 
-# DRAM traffic of the FP32 step kernel from one ncu capture
-# (profiles/ncu_k_step_fp32_tree.md), per site update, valid only while the
-# kernel sources are unchanged (SHA-256 of the files below).
+ELEM = {"fp32": 4, "bf16": 2, "fp16": 2, "fp64": 8}
+
+# DRAM traffic per site update from one ncu capture (profiles/), valid only
+# while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": None, "bytes_per_site": None}
+TRAFFIC = {"sha": None, "bytes_per_site": {}}
 
 
 def kernel_sha() -> str:
@@ -130,28 +139,60 @@ def set_bc(x, lat):
     workloads.apply_tree_bc(x, lat)
 
 
-def time_form(lat, precision, steps, warmup, torch, dist=None):
+def time_form(lat, precision, scheme, steps, warmup, torch, dist=None):
+    """Time `steps` launches with a CUDA event after each (solver stream).
+
+    Returns (total_ms, per-step durations in ms, solver time before the
+    first timed step)."""
     from paper_2202_11770_gb300 import hemegb
-    s = hemegb.Solver(lat, tau=0.55, precision=precision)
+    s = hemegb.Solver(lat, tau=0.55, precision=precision, scheme=scheme)
     set_bc(s, lat)
     s.init_equilibrium()
     s.step(warmup)
+    t_first = s.t
     stream = s.stream
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(steps)
-    e1.record(stream)
+    ev[0].record(stream)
+    for k in range(steps):
+        s.step(1)
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    total = ev[0].elapsed_time(ev[-1])
+    durs = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     mass, _ = s.reduce()
     assert math.isfinite(mass)
     del s
     torch.cuda.empty_cache()
-    return ms
+    return total, durs, t_first
+
+
+def form_stats(lat, precision, scheme, total, durs, t_first, steps, peak):
+    """MLUPS, algorithmic GB/s and per-kernel rooflines of one timed form."""
+    n = lat.n
+    e = ELEM[precision]
+    out = {"scheme": scheme, "mlups": n * steps / (total * 1e-3) / 1e6, "ms_per_step": total / steps}
+    if scheme == "ab":
+        b = bytes_per_site(e, "ab")
+        gbs = b * n / (total / steps * 1e-3) / 1e9
+        out.update(gbs=gbs, frac_of_measured_peak=gbs / peak, bytes_per_site=b,
+                   kernels={"k_step": {"launches": steps, "mean_us": total / steps * 1e3, "gbs": gbs,
+                                       "frac": gbs / peak, "bytes_per_site": b}})
+    else:
+        odd = [d for k, d in enumerate(durs) if (t_first + k) % 2 == 1]
+        even = [d for k, d in enumerate(durs) if (t_first + k) % 2 == 0]
+        b = bytes_per_site(e, "aa")
+        gbs = b * n / (total / steps * 1e-3) / 1e9
+        kern = {}
+        for name, ds, kb in (("k_aa_odd", odd, bytes_per_site(e, "aa_odd")),
+                             ("k_aa_even+fix", even, bytes_per_site(e, "aa_even"))):
+            m = sum(ds) / len(ds)
+            g = kb * n / (m * 1e-3) / 1e9
+            kern[name] = {"launches": len(ds), "mean_us": m * 1e3, "gbs": g, "frac": g / peak, "bytes_per_site": kb}
+        out.update(gbs=gbs, frac_of_measured_peak=gbs / peak, bytes_per_site=b, kernels=kern)
+    return out
 
 
 def e2e_job(lat, steps, torch):
@@ -189,29 +230,35 @@ def e2e_job(lat, steps, torch):
     return n * steps / dt / 1e6, h2d_step, d2h_step
 
 
-def adjoint_ratio(steps, torch):
+def adjoint_ratio(steps, torch, sites=2_000_000):
     """Adjoint (forward with sqrt(N) checkpoints + recompute + reverse) vs
     forward-only time over the same N steps: seeded depth-4 tree, ~2M sites,
     64 inlet amplitude groups, FP32."""
     from paper_2202_11770_gb300 import hemegb, workloads
-    lat, obj = workloads.adjoint_case()
-    s = hemegb.Solver(lat, tau=0.55, precision="fp32")
+    lat, obj = workloads.adjoint_case(target_sites=sites)
+    fwd = {}
+    for sch in ("ab", "aa"):
+        s = hemegb.Solver(lat, tau=0.55, precision="fp32", scheme=sch)
+        workloads.apply_tree_bc(s, lat)
+        s.init_equilibrium()
+        s.step(10)
+        s.init_equilibrium()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        fwd[sch] = e0.elapsed_time(e1)
+        del s
+    s = hemegb.Solver(lat, tau=0.55, precision="fp32", scheme="auto")
     workloads.apply_tree_bc(s, lat)
     ws = s.adjoint_workspace(steps, obj.sites.size)
-    s.init_equilibrium()
-    s.step(10)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.init_equilibrium()
-    e0.record(s.stream)
-    s.step(steps)
-    e1.record(s.stream)
-    torch.cuda.synchronize()
-    fwd = e0.elapsed_time(e1)
     s.init_equilibrium()
     s.adjoint(min(steps, 50), obj.sites, obj.target, obj.axis, workspace=ws)   # warm-up
     s.init_equilibrium()
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(s.stream)
     J, dtau, damp = s.adjoint(steps, obj.sites, obj.target, obj.axis, workspace=ws)
     e1.record(s.stream)
@@ -219,7 +266,8 @@ def adjoint_ratio(steps, torch):
     adj = e0.elapsed_time(e1)
     K = int(math.ceil(math.sqrt(steps)))
     out = {"workload": "seeded depth-4 tree, 64 inlet amplitude groups, FP32", "n_sites": lat.n, "steps": steps,
-           "checkpoint_interval": K, "forward_ms": fwd, "adjoint_ms": adj, "ratio": adj / fwd,
+           "checkpoint_interval": K, "forward_ms": fwd, "adjoint_ms": adj,
+           "ratio": adj / min(fwd.values()), "ratio_vs_pull_ab": adj / fwd["ab"],
            "J": J, "dJ_dtau": dtau, "probe_sites": int(obj.sites.size),
            "adjoint_workspace_gb": ws[2] / 1e9}
     del s, ws
@@ -286,9 +334,10 @@ def run_ours(args):
     n = lat.n
     peak, peak_kind = measured_peaks()
 
+    scheme = args.scheme
     clocks = ClockSampler(local)
     clocks.start()
-    ms = time_form(lat, "fp32", args.steps, args.warmup, torch, dist)
+    ms, durs, t_first = time_form(lat, "fp32", scheme, args.steps, args.warmup, torch, dist)
     clk = clocks.stop()
     if dist is not None:
         t = torch.tensor([ms], device="cuda")
@@ -296,23 +345,21 @@ def run_ours(args):
         ms = float(t.item())
     total_updates = n * args.steps * world
     value = total_updates / (ms * 1e-3) / 1e6
-    per_launch_s = ms * 1e-3 / args.steps
-    alg = bytes_per_site(4) * n
-    achieved = alg / per_launch_s / 1e9
+    head = form_stats(lat, "fp32", scheme, ms, durs, t_first, args.steps, peak)
+    kname = "k_step" if scheme == "ab" else "k_aa_odd"
+    kst = head["kernels"][kname]
     traffic = None
-    if TRAFFIC["sha"] == kernel_sha() and TRAFFIC["bytes_per_site"]:
-        traffic = TRAFFIC["bytes_per_site"] * n
+    if TRAFFIC["sha"] == kernel_sha() and kname in TRAFFIC["bytes_per_site"]:
+        traffic = TRAFFIC["bytes_per_site"][kname] * n
 
-    forms = {}
+    forms = {f"fp32_{scheme}": head}
     if not args.quick:
-        for prec in ("bf16", "fp16"):
-            msf = time_form(lat, prec, args.steps, args.warmup, torch, dist)
-            gbs = bytes_per_site(2) * n / (msf * 1e-3 / args.steps) / 1e9
-            forms[prec] = {"mlups": n * args.steps / (msf * 1e-3) / 1e6, "ms_per_step": msf / args.steps,
-                           "gbs": gbs, "frac_of_measured_peak": gbs / peak, "bytes_per_site": bytes_per_site(2)}
-        forms["fp32"] = {"mlups": n * args.steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / args.steps,
-                         "gbs": achieved, "frac_of_measured_peak": achieved / peak,
-                         "bytes_per_site": bytes_per_site(4)}
+        for prec in ("fp32", "bf16", "fp16"):
+            for sch in ("ab", "aa"):
+                if f"{prec}_{sch}" in forms:
+                    continue
+                tot, d, tf = time_form(lat, prec, sch, args.steps, args.warmup, torch, dist)
+                forms[f"{prec}_{sch}"] = form_stats(lat, prec, sch, tot, d, tf, args.steps, peak)
 
     adjoint = None
     if not args.quick and args.adjoint_steps > 0:
@@ -335,16 +382,19 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_sites": n, "tau": 0.55, "scheme": "pull A-B",
+            "config": {"workload": WORKLOAD, "n_sites": n, "tau": 0.55,
+                       "scheme": {"ab": "pull A-B", "aa": "AA pattern"}[scheme],
                        "parallelism": f"replicas x{world}", "l2": "working set 4.5 GB/step >> 129 MB L2, no flush",
                        "fill": round(lat.info["fill"], 4)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_step<float,gather>", "algorithmic_bytes_per_site": bytes_per_site(4)},
+            "roofline": {"bound": "hbm", "achieved": kst["gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": kst["gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": kname + "<float>", "launches": kst["launches"], "mean_us": kst["mean_us"],
+                         "algorithmic_bytes_per_site": kst["bytes_per_site"],
+                         "step_gbs": head["gbs"], "step_bytes_per_site": head["bytes_per_site"]},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps if scheme == "ab" else args.steps + head["kernels"]["k_aa_even+fix"]["launches"],
             "forms": forms,
             "adjoint": adjoint,
         }
@@ -364,14 +414,22 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2000)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-sites", type=int, default=2_000_000)
+    ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint/forward timing")
     ap.add_argument("--ref-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="FP32 only, no e2e (profiling runs)")
+    ap.add_argument("--scheme", default="aa", choices=["ab", "aa"],
+                    help="streaming scheme of the headline FP32 form (the solver's AUTO choice is aa)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.adjoint_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"adjoint": adjoint_ratio(args.adjoint_steps, torch, args.adjoint_sites)}))
     else:
         run_ours(args)
 

@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 
 import numpy as np
 
@@ -37,7 +38,9 @@ _I64 = C.POINTER(C.c_int64)
 def _load():
     global _lib
     if _lib is None:
-        lib = C.CDLL(str(_build.build()))
+        # HLB_ORACLE_LIB lets the mutation test load a deliberately broken copy
+        path = os.environ.get("HLB_ORACLE_LIB") or str(_build.build())
+        lib = C.CDLL(path)
         lib.ora_create.argtypes = [C.c_int64, _I32, _I32, C.c_int, _I32, _D, _D, _D, _I32, _I32,
                                    C.POINTER(_P)]
         lib.ora_free.argtypes = [_P]

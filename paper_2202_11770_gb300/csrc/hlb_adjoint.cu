@@ -48,128 +48,159 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// One reverse step at time t (GPREV: f(t) is gathered from s'(t-1); false
-// only at t = 0 where prev holds f(0) itself).
-template <typename S, bool GPREV>
-__global__ void __launch_bounds__(BLOCK) k_adjoint(const S* __restrict__ prev, const S* __restrict__ cur,
-                                                   const S* __restrict__ mu_next, S* __restrict__ mu_out,
-                                                   const int32_t* __restrict__ src,
-                                                   const LinkRec* __restrict__ links,
-                                                   const double* __restrict__ amp, const AdjParams ap,
-                                                   double* __restrict__ dtau_part, double* __restrict__ dlink,
-                                                   int store) {
+// Adjoint of one reverse step at site x (GPREV: f(t) is gathered from
+// s'(t-1); false only at t = 0 where prev holds f(0) itself).  With
+// IOLET = false the site is skipped (returns false) when it has an iolet
+// link; those sites go through the IOLET = true instantiation, which adds
+// the boundary transposes.  Returns the site's dJ/dtau contribution in *dtau.
+template <typename S, bool GPREV, bool IOLET>
+__device__ __forceinline__ bool adjoint_site(const S* __restrict__ prev, const S* __restrict__ cur,
+                                             const S* __restrict__ mu_next, S* __restrict__ mu_out,
+                                             const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
+                                             const double* __restrict__ amp, const AdjParams& ap,
+                                             double* __restrict__ dlink, int store, int64_t x, double* dtau) {
   using R = typename Real<S>::type;
-  __shared__ double sh[BLOCK / 32];
   const StepParams& p = ap.prev;
   const int64_t n = p.n;
-  const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-  double dtau_local = 0;
-  if (x < n) {
-    R h[Q], lam[Q];
-    bool any_iolet = false;
-    h[0] = ldpop(prev + x);
-    lam[0] = ldpop(mu_next + x);
+  R h[Q], lam[Q];
+  bool any_iolet = false;
+  h[0] = ldpop(prev + x);
+  lam[0] = ldpop(mu_next + x);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int32_t s = ldidx(src + (int64_t)(i - 1) * n + x);
-      if (GPREV) h[i] = ldpop(prev + (s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x));
-      else h[i] = ldpop(prev + (int64_t)i * n + x);
-      // s'_opp(i)(x) is read by x - c_i = x + c_opp(i) in direction opp(i),
-      // or by x itself in direction i when that source is not fluid
-      lam[opp(i)] = ldpop(mu_next + (s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x));
-      any_iolet |= s <= -2;
-    }
-    if (any_iolet) {
-      if (GPREV) iolet_fixup<S>(prev, src, links, amp, p, x, h);
-      // boundary terms of G_t, which reads the moments of s'(t) at x
-      R d = R(0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        R v = ldpop(cur + (int64_t)i * n + x);
-        d += v;
-        if (cx(i)) jx += cx(i) > 0 ? v : -v;
-        if (cy(i)) jy += cy(i) > 0 ? v : -v;
-        if (cz(i)) jz += cz(i) > 0 ? v : -v;
-      }
-      const R rho_s = R(1) + d;
-      const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
-      R gsum = R(0), gux = R(0), guy = R(0), guz = R(0);
-#pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int32_t s = src[(int64_t)(i - 1) * n + x];
-        if (s > -2) continue;
-        const int64_t r = -s - 2;
-        const LinkRec L = links[r];
-        const R a = ldpop(mu_next + (int64_t)i * n + x);  // adjoint of f_i(x, t+1)
-        const R val = R(ap.val_cur[L.iolet]);
-        if (L.kind == 0) {
-          const R rho = p.ladd_rho_one ? R(1) : rho_s;
-          if (!p.ladd_rho_one) gsum += a * R(L.coef) * R(amp[L.group]) * val;
-          dlink[r] += (double)(a * R(L.coef) * rho * val);
-        } else {
-          lam[opp(i)] = R(0);  // the ghost value does not read s'_opp(i)(x)
-          const IoletParam io = p.io[L.iolet];
-          R gx = ux, gy = uy, gz = uz;
-          if (!p.ghost_full_u) {
-            const R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
-            gx = un * R(io.nx);
-            gy = un * R(io.ny);
-            gz = un * R(io.nz);
-          }
-          const R rho_k = R(1) + val;
-          const R cu = cdotu<R>(i, gx, gy, gz);
-          const R k3 = a * wgt<R>(i) * rho_k;
-          // d f^eq_i / d u_g = w_i rho_k (3 c_i + 9 (c_i . u_g) c_i - 3 u_g)
-          R vx = k3 * (R(3) * cx(i) + R(9) * cu * cx(i) - R(3) * gx);
-          R vy = k3 * (R(3) * cy(i) + R(9) * cu * cy(i) - R(3) * gy);
-          R vz = k3 * (R(3) * cz(i) + R(9) * cu * cz(i) - R(3) * gz);
-          if (!p.ghost_full_u) {
-            const R vn = vx * R(io.nx) + vy * R(io.ny) + vz * R(io.nz);
-            vx = vn * R(io.nx);
-            vy = vn * R(io.ny);
-            vz = vn * R(io.nz);
-          }
-          gux += vx;
-          guy += vy;
-          guz += vz;
-        }
-      }
-      // d u_s / d s'_j = (c_j - u_s) / rho_s;  d rho_s / d s'_j = 1
-#pragma unroll
-      for (int j = 0; j < Q; ++j)
-        lam[j] += gsum + ((R(cx(j)) - ux) * gux + (R(cy(j)) - uy) * guy + (R(cz(j)) - uz) * guz) / rho_s;
-    }
-    // collision adjoint at f(t) = h
-    const Macro<R> m = moments<R>(h);
-    const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-    const R omega = R(p.omega);
-    R S0 = R(0), Lw = R(0), Bx = R(0), By = R(0), Bz = R(0), dt = R(0);
+  for (int i = 1; i < Q; ++i) {
+    const int32_t s = ldidx(src + (int64_t)(i - 1) * n + x);
+    if (GPREV) h[i] = ldpop(prev + (s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x));
+    else h[i] = ldpop(prev + (int64_t)i * n + x);
+    // s'_opp(i)(x) is read by x - c_i = x + c_opp(i) in direction opp(i),
+    // or by x itself in direction i when that source is not fluid
+    lam[opp(i)] = ldpop(mu_next + (s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x));
+    any_iolet |= s <= -2;
+  }
+  if (!IOLET && any_iolet) return false;
+  if (IOLET) {
+    if (GPREV) iolet_fixup<S>(prev, src, links, amp, p, x, h);
+    // boundary terms of G_t, which reads the moments of s'(t) at x
+    R d = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const R cu = cdotu<R>(i, m.ux, m.uy, m.uz);
-      const R w = wgt<R>(i);
-      S0 += lam[i] * w * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15);  // feq_i / rho
-      Lw += lam[i] * w;
-      const R b = lam[i] * w * (R(3) + R(9) * cu);
-      if (cx(i)) Bx += cx(i) > 0 ? b : -b;
-      if (cy(i)) By += cy(i) > 0 ? b : -b;
-      if (cz(i)) Bz += cz(i) > 0 ? b : -b;
-      dt += lam[i] * (h[i] - heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15));
+      R v = ldpop(cur + (int64_t)i * n + x);
+      d += v;
+      if (cx(i)) jx += cx(i) > 0 ? v : -v;
+      if (cy(i)) jy += cy(i) > 0 ? v : -v;
+      if (cz(i)) jz += cz(i) > 0 ? v : -v;
     }
-    // (1/rho) d feq_i/d u_a summed with lam: B_a - 3 u_a Lw
-    Bx -= R(3) * m.ux * Lw;
-    By -= R(3) * m.uy * Lw;
-    Bz -= R(3) * m.uz * Lw;
-    dtau_local = (double)(omega * omega * dt);
-    if (store) {
+    const R rho_s = R(1) + d;
+    const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
+    R gsum = R(0), gux = R(0), guy = R(0), guz = R(0);
 #pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        const R v = (R(1) - omega) * lam[j] +
-                    omega * (S0 + (R(cx(j)) - m.ux) * Bx + (R(cy(j)) - m.uy) * By + (R(cz(j)) - m.uz) * Bz);
-        mu_out[(int64_t)j * n + x] = from_real<S>(v);
+    for (int i = 1; i < Q; ++i) {
+      const int32_t s = src[(int64_t)(i - 1) * n + x];
+      if (s > -2) continue;
+      const int64_t r = -s - 2;
+      const LinkRec L = links[r];
+      const R a = ldpop(mu_next + (int64_t)i * n + x);  // adjoint of f_i(x, t+1)
+      const R val = R(ap.val_cur[L.iolet]);
+      if (L.kind == 0) {
+        const R rho = p.ladd_rho_one ? R(1) : rho_s;
+        if (!p.ladd_rho_one) gsum += a * R(L.coef) * R(amp[L.group]) * val;
+        dlink[r] += (double)(a * R(L.coef) * rho * val);
+      } else {
+        lam[opp(i)] = R(0);  // the ghost value does not read s'_opp(i)(x)
+        const IoletParam io = p.io[L.iolet];
+        R gx = ux, gy = uy, gz = uz;
+        if (!p.ghost_full_u) {
+          const R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
+          gx = un * R(io.nx);
+          gy = un * R(io.ny);
+          gz = un * R(io.nz);
+        }
+        const R rho_k = R(1) + val;
+        const R cu = cdotu<R>(i, gx, gy, gz);
+        const R k3 = a * wgt<R>(i) * rho_k;
+        // d f^eq_i / d u_g = w_i rho_k (3 c_i + 9 (c_i . u_g) c_i - 3 u_g)
+        R vx = k3 * (R(3) * cx(i) + R(9) * cu * cx(i) - R(3) * gx);
+        R vy = k3 * (R(3) * cy(i) + R(9) * cu * cy(i) - R(3) * gy);
+        R vz = k3 * (R(3) * cz(i) + R(9) * cu * cz(i) - R(3) * gz);
+        if (!p.ghost_full_u) {
+          const R vn = vx * R(io.nx) + vy * R(io.ny) + vz * R(io.nz);
+          vx = vn * R(io.nx);
+          vy = vn * R(io.ny);
+          vz = vn * R(io.nz);
+        }
+        gux += vx;
+        guy += vy;
+        guz += vz;
       }
     }
+    // d u_s / d s'_j = (c_j - u_s) / rho_s;  d rho_s / d s'_j = 1
+#pragma unroll
+    for (int j = 0; j < Q; ++j)
+      lam[j] += gsum + ((R(cx(j)) - ux) * gux + (R(cy(j)) - uy) * guy + (R(cz(j)) - uz) * guz) / rho_s;
   }
+  // collision adjoint at f(t) = h
+  const Macro<R> m = moments<R>(h);
+  const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+  const R omega = R(p.omega);
+  R S0 = R(0), Lw = R(0), Bx = R(0), By = R(0), Bz = R(0), dt = R(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const R cu = cdotu<R>(i, m.ux, m.uy, m.uz);
+    const R w = wgt<R>(i);
+    S0 += lam[i] * w * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15);  // feq_i / rho
+    Lw += lam[i] * w;
+    const R b = lam[i] * w * (R(3) + R(9) * cu);
+    if (cx(i)) Bx += cx(i) > 0 ? b : -b;
+    if (cy(i)) By += cy(i) > 0 ? b : -b;
+    if (cz(i)) Bz += cz(i) > 0 ? b : -b;
+    dt += lam[i] * (h[i] - heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15));
+  }
+  // (1/rho) d feq_i/d u_a summed with lam: B_a - 3 u_a Lw
+  Bx -= R(3) * m.ux * Lw;
+  By -= R(3) * m.uy * Lw;
+  Bz -= R(3) * m.uz * Lw;
+  *dtau = (double)(omega * omega * dt);
+  if (store) {
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      const R v = (R(1) - omega) * lam[j] +
+                  omega * (S0 + (R(cx(j)) - m.ux) * Bx + (R(cy(j)) - m.uy) * By + (R(cz(j)) - m.uz) * Bz);
+      mu_out[(int64_t)j * n + x] = from_real<S>(v);
+    }
+  }
+  return true;
+}
+
+// Bulk reverse step over all sites without iolet links.
+template <typename S, bool GPREV>
+__global__ void __launch_bounds__(BLOCK) k_adjoint(const S* __restrict__ prev, const S* __restrict__ mu_next,
+                                                   S* __restrict__ mu_out, const int32_t* __restrict__ src,
+                                                   const AdjParams ap, double* __restrict__ dtau_part, int store) {
+  __shared__ double sh[BLOCK / 32];
+  const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  double dtau_local = 0;
+  if (x < ap.prev.n)
+    adjoint_site<S, GPREV, false>(prev, nullptr, mu_next, mu_out, src, nullptr, nullptr, ap, nullptr, store, x,
+                                  &dtau_local);
+  const double bs = block_sum(dtau_local, sh);
+  if (threadIdx.x == 0) dtau_part[blockIdx.x] += bs;
+}
+
+// Reverse step of the sites with iolet links (one thread per site).
+template <typename S, bool GPREV>
+__global__ void __launch_bounds__(128) k_adjoint_iolet(const S* __restrict__ prev, const S* __restrict__ cur,
+                                                       const S* __restrict__ mu_next, S* __restrict__ mu_out,
+                                                       const int32_t* __restrict__ src,
+                                                       const LinkRec* __restrict__ links,
+                                                       const double* __restrict__ amp, const AdjParams ap,
+                                                       const int32_t* __restrict__ sites, int64_t nsites,
+                                                       double* __restrict__ dtau_part, double* __restrict__ dlink,
+                                                       int store) {
+  __shared__ double sh[4];
+  const int64_t q = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  double dtau_local = 0;
+  if (q < nsites)
+    adjoint_site<S, GPREV, true>(prev, cur, mu_next, mu_out, src, links, amp, ap, dlink, store, sites[q],
+                                 &dtau_local);
   const double bs = block_sum(dtau_local, sh);
   if (threadIdx.x == 0) dtau_part[blockIdx.x] += bs;
 }
@@ -257,14 +288,24 @@ cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, co
   ap.prev = h->params(tb_prev);
   StepParams pc = h->params(tb_cur);
   for (int k = 0; k < MAX_IOLETS; ++k) ap.val_cur[k] = k < h->n_iolets ? pc.io[k].val : 0.0;
-  if (gprev)
-    k_adjoint<S, true><<<grid_for(h->n), BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
-                                                         h->d_src, h->d_links, h->d_amp, ap, dtau_part, dlink,
-                                                         store ? 1 : 0);
-  else
-    k_adjoint<S, false><<<grid_for(h->n), BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
-                                                          h->d_src, h->d_links, h->d_amp, ap, dtau_part, dlink,
-                                                          store ? 1 : 0);
+  const int st_ = store ? 1 : 0;
+  double* part_i = dtau_part + grid_for(h->n);  // partials of the iolet-site kernel
+  const unsigned gi = (unsigned)((h->n_iolet_sites + 127) / 128);
+  if (gprev) {
+    k_adjoint<S, true><<<grid_for(h->n), BLOCK, 0, st>>>((const S*)prev, (const S*)mu_next, (S*)mu_out, h->d_src, ap,
+                                                         dtau_part, st_);
+    if (gi)
+      k_adjoint_iolet<S, true><<<gi, 128, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
+                                                   h->d_src, h->d_links, h->d_amp, ap, h->d_iolet_sites,
+                                                   h->n_iolet_sites, part_i, dlink, st_);
+  } else {
+    k_adjoint<S, false><<<grid_for(h->n), BLOCK, 0, st>>>((const S*)prev, (const S*)mu_next, (S*)mu_out, h->d_src, ap,
+                                                          dtau_part, st_);
+    if (gi)
+      k_adjoint_iolet<S, false><<<gi, 128, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
+                                                    h->d_src, h->d_links, h->d_amp, ap, h->d_iolet_sites,
+                                                    h->n_iolet_sites, part_i, dlink, st_);
+  }
   return cudaGetLastError();
 }
 
@@ -323,7 +364,7 @@ AdjLayout adj_layout(const hlb_solver* h, int64_t N, int64_t np) {
   y.ck = off; off += st * (size_t)y.nck;
   y.seg = off; off += st * (size_t)y.nseg;
   y.mu = off; off += st * 2;
-  y.dtau = off; off += al256(sizeof(double) * grid_for(h->n));
+  y.dtau = off; off += al256(sizeof(double) * (grid_for(h->n) + (size_t)(h->n_iolet_sites + 127) / 128));
   y.dlink = off; off += al256(sizeof(double) * (size_t)std::max<int64_t>(h->n_links, 1));
   y.sites = off; off += al256(sizeof(int64_t) * (size_t)std::max<int64_t>(np, 1));
   y.target = off; off += al256(sizeof(double) * (size_t)std::max<int64_t>(np, 1));
@@ -349,7 +390,7 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   double* jp = (double*)(ws + y.jp);
   int64_t* gbegin = (int64_t*)(ws + y.gbegin);
   double* out = (double*)(ws + y.out);
-  const int64_t nb = grid_for(h->n);
+  const int64_t nb = grid_for(h->n) + (h->n_iolet_sites + 127) / 128;  // bulk + iolet-site partials
   const int64_t np = obj->n_probe;
   const int G = h->n_groups_total;
 
@@ -360,10 +401,10 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   } while (0)
 
   // starting pre-collision state f(t0) into checkpoint 0
-  if (h->phase == 0)
+  if (h->phase == HLB_READ_LOCAL)
     TRY(cudaMemcpyAsync(ck(0), h->f[h->cur], h->state_bytes(), cudaMemcpyDeviceToDevice, st));
   else
-    TRY(hlb_launch_state(h, h->f[h->cur], true, h->t - 1, ck(0), st));
+    TRY(hlb_launch_state(h, h->f[h->cur], h->phase, h->t - 1, ck(0), -1, st));
   const int64_t t0 = h->t;
   TRY(cudaMemsetAsync(dtau_part, 0, sizeof(double) * nb, st));
   TRY(cudaMemsetAsync(dlink, 0, sizeof(double) * std::max<int64_t>(h->n_links, 1), st));
@@ -424,15 +465,20 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   k_adj_finish<<<2 + G, 256, 0, st>>>(jp, np, dtau_part, nb, dlink, gbegin, G, out);
   TRY(cudaGetLastError());
 
-  // leave the solver at t0 + N with the last post-collision state
+  // leave the solver at t0 + N: A-B keeps the last post-collision state,
+  // AA receives the gathered pre-collision state f(t0 + N) in place
   const void* last = sg(N - 1 - last_begin);
-  TRY(cudaMemcpyAsync(h->f[0], last, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+  if (h->scheme == HLB_AA)
+    TRY(hlb_launch_state(h, last, HLB_READ_GATHER_AB, t0 + N - 1, h->f[0], -1, st));
+  else
+    TRY(cudaMemcpyAsync(h->f[0], last, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
   std::vector<double> host(2 + G);
   TRY(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
 #undef TRY
   h->cur = 0;
-  h->phase = 1;
+  h->phase = h->scheme == HLB_AA ? HLB_READ_LOCAL : HLB_READ_GATHER_AB;
+  h->stepped = h->scheme != HLB_AA;
   h->t = t0 + N;
   if (J) *J = host[0];
   if (dtau_out) *dtau_out = host[1];

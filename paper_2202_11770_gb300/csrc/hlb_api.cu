@@ -107,14 +107,15 @@ StepParams hlb_solver::params(int64_t tb) const {
 namespace {
 
 struct Layout {
-  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, total = 0;
+  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, total = 0;
   int64_t n_links = 0;
   int32_t n_groups = 0;
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 
-int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* per_iolet_links) {
+int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* per_iolet_links,
+             int64_t* n_iolet_sites) {
   if (!L || !o) return hlb_fail(HLB_ERR_ARG, "null lattice or options");
   if (L->n_sites < 1 || L->n_sites >= ((int64_t)1 << 31)) return hlb_fail(HLB_ERR_ARG, "n_sites must be in [1, 2^31)");
   if (!L->src || !L->xyz) return hlb_fail(HLB_ERR_ARG, "lattice needs xyz and src");
@@ -123,7 +124,6 @@ int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* p
   if (o->precision < HLB_FP32 || o->precision > HLB_FP64) return hlb_fail(HLB_ERR_ARG, "unknown precision");
   if (o->scheme != HLB_SCHEME_AUTO && o->scheme != HLB_PULL_AB && o->scheme != HLB_AA)
     return hlb_fail(HLB_ERR_ARG, "unknown scheme");
-  if (o->scheme == HLB_AA) return hlb_fail(HLB_ERR_ARG, "scheme HLB_AA is not available in this build");
   for (int k = 0; k < L->n_iolets; ++k) {
     const hlb_iolet& io = L->iolets[k];
     if (io.kind != HLB_VELOCITY && io.kind != HLB_PRESSURE) return hlb_fail(HLB_ERR_ARG, "bad iolet kind");
@@ -134,6 +134,7 @@ int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* p
   }
   const int64_t n = L->n_sites;
   per_iolet_links->assign((size_t)std::max(1, (int)L->n_iolets), 0);
+  std::vector<uint8_t> iolet_site((size_t)n, 0);
   for (int i = 1; i < Q; ++i) {
     const int32_t* row = L->src + (int64_t)(i - 1) * n;
     for (int64_t x = 0; x < n; ++x) {
@@ -148,13 +149,21 @@ int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* p
           if (g < 0 || g >= L->iolets[k].n_groups) return hlb_fail(HLB_ERR_ARG, "amplitude group out of range");
         }
         (*per_iolet_links)[k]++;
+        iolet_site[x] = 1;
       }
     }
   }
+  *n_iolet_sites = 0;
+  for (int64_t x = 0; x < n; ++x) *n_iolet_sites += iolet_site[x];
   return HLB_OK;
 }
 
-Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int64_t>& per_iolet) {
+// AUTO resolves to the scheme measured faster on GB300: the AA pattern moves
+// 188 B per FP32 site update against 224 B for pull A-B.
+int32_t resolve_scheme(int32_t scheme) { return scheme == HLB_SCHEME_AUTO ? HLB_AA : scheme; }
+
+Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int64_t>& per_iolet,
+              int64_t n_iolet_sites) {
   Layout y;
   const int64_t n = L->n_sites;
   size_t eb = o->precision == HLB_FP64 ? 8 : (o->precision == HLB_FP32 ? 4 : 2);
@@ -164,13 +173,15 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
     if (L->iolets[k].kind == HLB_VELOCITY) y.n_groups += L->iolets[k].n_groups;
   size_t off = 0;
   y.f0 = off; off += state;
-  y.f1 = off; off += state;
+  y.f1 = off; off += resolve_scheme(o->scheme) == HLB_AA ? 0 : state;
   y.src = off; off += align_up(sizeof(int32_t) * 18 * (size_t)n);
   y.links = off; off += align_up(sizeof(LinkRec) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.amp = off; off += align_up(sizeof(double) * (size_t)std::max(y.n_groups, 1));
   y.normal = off; off += L->wall_normal ? align_up(sizeof(float) * 3 * (size_t)n) : 0;
   y.stage = off; off += align_up(sizeof(float) * 5 * (size_t)n);
   y.red = off; off += align_up(sizeof(double) * (size_t)hlb_reduce_slots(n, L->n_iolets));
+  y.lflux = off; off += align_up(sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1));
+  y.isites = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(n_iolet_sites, 1));
   y.total = off;
   return y;
 }
@@ -180,9 +191,10 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
 extern "C" int hlb_workspace_bytes(const hlb_lattice* L, const hlb_options* o, size_t* bytes) {
   if (!bytes) return hlb_fail(HLB_ERR_ARG, "null output");
   std::vector<int64_t> per;
-  int rc = validate(L, o, &per);
+  int64_t nis = 0;
+  int rc = validate(L, o, &per, &nis);
   if (rc) return rc;
-  *bytes = layout(L, o, per).total;
+  *bytes = layout(L, o, per, nis).total;
   return HLB_OK;
 }
 
@@ -191,9 +203,10 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   if (!out) return hlb_fail(HLB_ERR_ARG, "null output");
   *out = nullptr;
   std::vector<int64_t> per;
-  int rc = validate(L, o, &per);
+  int64_t nis = 0;
+  int rc = validate(L, o, &per, &nis);
   if (rc) return rc;
-  Layout y = layout(L, o, per);
+  Layout y = layout(L, o, per, nis);
   if (!ws) return hlb_fail(HLB_ERR_WS, "null workspace");
   if (((uintptr_t)ws & 255) != 0) return hlb_fail(HLB_ERR_WS, "workspace must be 256-byte aligned");
   if (ws_bytes < y.total)
@@ -211,7 +224,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->n_iolets = L->n_iolets;
   h->iolets.assign(L->iolets, L->iolets + L->n_iolets);
   h->precision = o->precision;
-  h->scheme = HLB_PULL_AB;
+  h->scheme = resolve_scheme(o->scheme);
   h->ladd_rho_one = o->ladd_rho_one ? 1 : 0;
   h->ghost_full_u = o->ghost_full_u ? 1 : 0;
   h->stream = (cudaStream_t)stream;
@@ -234,7 +247,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
 
   char* base = (char*)ws;
   h->f[0] = base + y.f0;
-  h->f[1] = base + y.f1;
+  h->f[1] = h->scheme == HLB_AA ? nullptr : base + y.f1;
   h->d_src = (int32_t*)(base + y.src);
   h->d_links = (LinkRec*)(base + y.links);
   h->d_amp = (double*)(base + y.amp);
@@ -242,6 +255,9 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->d_stage = (float*)(base + y.stage);
   h->d_red = (double*)(base + y.red);
   h->red_slots = hlb_reduce_slots(n, h->n_iolets);
+  h->d_lflux = (double*)(base + y.lflux);
+  h->d_iolet_sites = (int32_t*)(base + y.isites);
+  h->n_iolet_sites = nis;
 
   // link records sorted by (iolet, group, site, direction)
   std::vector<int64_t> bucket_base(h->n_iolets + 1, 0);
@@ -306,9 +322,17 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
     }
 
   cudaStream_t st = h->stream;
-  int64_t nb = (n + 255) / 256;
+  int64_t nb = hlb_reduce_partials(n);
   std::vector<int64_t> begin(h->link_begin);
   std::vector<double> ampf(std::max(g, 1), 0.0);
+  std::vector<int32_t> isites;
+  isites.reserve((size_t)nis);
+  for (int64_t x = 0; x < n; ++x)
+    for (int i = 1; i < Q; ++i)
+      if (L->src[(int64_t)(i - 1) * n + x] <= -2) {
+        isites.push_back((int32_t)x);
+        break;
+      }
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * 18 * (size_t)n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && y.n_links > 0)
@@ -318,6 +342,9 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
     e = cudaMemcpyAsync(h->d_normal, L->wall_normal, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->d_red + nb, begin.data(), sizeof(int64_t) * begin.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nis > 0)
+    e = cudaMemcpyAsync(h->d_iolet_sites, isites.data(), sizeof(int32_t) * (size_t)nis, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_lflux, 0, sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->state_bytes(), st);  // rest: h = f - w = 0
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -392,8 +419,9 @@ extern "C" int hlb_init_equilibrium(hlb_solver* h, double rho0, const float* u0,
   }
   CUDA_TRY(hlb_launch_init(h, h->f[0], rho0, du, h->stream));
   h->cur = 0;
-  h->phase = 0;
+  h->phase = HLB_READ_LOCAL;
   h->t = 0;
+  h->stepped = false;
   if (u0 && where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
   return HLB_OK;
 }
@@ -402,11 +430,19 @@ extern "C" int hlb_step(hlb_solver* h, int64_t nsteps) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
   if (nsteps < 0) return hlb_fail(HLB_ERR_ARG, "negative step count");
   for (int64_t s = 0; s < nsteps; ++s) {
-    const bool gather = h->phase == 1;
-    CUDA_TRY(hlb_launch_step(h, h->f[h->cur], h->f[h->cur ^ 1], gather, h->t - 1, h->stream));
-    h->cur ^= 1;
-    h->phase = 1;
+    if (h->scheme == HLB_AA) {
+      // even step from f(t) in place, odd step from the swapped buffer
+      const bool odd = h->phase == HLB_READ_GATHER_AA;
+      CUDA_TRY(hlb_launch_aa(h, h->f[0], odd, h->t, h->stream));
+      h->phase = odd ? HLB_READ_LOCAL : HLB_READ_GATHER_AA;
+    } else {
+      const bool gather = h->phase == HLB_READ_GATHER_AB;
+      CUDA_TRY(hlb_launch_step(h, h->f[h->cur], h->f[h->cur ^ 1], gather, h->t - 1, h->stream));
+      h->cur ^= 1;
+      h->phase = HLB_READ_GATHER_AB;
+    }
     h->t += 1;
+    h->stepped = true;
   }
   return HLB_OK;
 }
@@ -420,15 +456,14 @@ extern "C" int hlb_time(const hlb_solver* h, int64_t* t) {
 extern "C" int hlb_read_macros(hlb_solver* h, float* rho, float* u, float* wss, int32_t where) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
   const int64_t n = h->n;
-  const bool gather = h->phase == 1;
   if (where == HLB_DEVICE) {
-    CUDA_TRY(hlb_launch_macros(h, h->f[h->cur], gather, h->t - 1, rho, u, wss, h->stream));
+    CUDA_TRY(hlb_launch_macros(h, h->f[h->cur], h->phase, h->t - 1, rho, u, wss, h->stream));
     return HLB_OK;
   }
   float* sr = rho ? h->d_stage : nullptr;
   float* su = u ? h->d_stage + n : nullptr;
   float* sw = wss ? h->d_stage + 4 * n : nullptr;
-  CUDA_TRY(hlb_launch_macros(h, h->f[h->cur], gather, h->t - 1, sr, su, sw, h->stream));
+  CUDA_TRY(hlb_launch_macros(h, h->f[h->cur], h->phase, h->t - 1, sr, su, sw, h->stream));
   if (rho) CUDA_TRY(cudaMemcpyAsync(rho, sr, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
   if (u) CUDA_TRY(cudaMemcpyAsync(u, su, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
   if (wss) CUDA_TRY(cudaMemcpyAsync(wss, sw, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
@@ -438,9 +473,9 @@ extern "C" int hlb_read_macros(hlb_solver* h, float* rho, float* u, float* wss, 
 
 extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
-  const int64_t nb = (h->n + 255) / 256;
+  const int64_t nb = hlb_reduce_partials(h->n);
   double* out = h->d_red + nb + (h->n_iolets + 1);
-  CUDA_TRY(hlb_launch_reduce(h, h->f[h->cur], h->phase == 1, h->t - 1, out, h->stream));
+  CUDA_TRY(hlb_launch_reduce(h, h->f[h->cur], h->phase, h->t - 1, h->stepped, out, h->stream));
   std::vector<double> host(1 + h->n_iolets);
   CUDA_TRY(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -454,16 +489,23 @@ extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
 extern "C" int hlb_get_state(hlb_solver* h, void* f, int32_t where, int64_t* t) {
   if (!h || !f) return hlb_fail(HLB_ERR_ARG, "null argument");
   const size_t bytes = h->state_bytes();
-  if (h->phase == 0) {
+  if (h->phase == HLB_READ_LOCAL) {
     CUDA_TRY(cudaMemcpyAsync(f, h->f[h->cur], bytes, where == HLB_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                              h->stream));
   } else if (where == HLB_DEVICE) {
-    CUDA_TRY(hlb_launch_state(h, h->f[h->cur], true, h->t - 1, f, h->stream));
-  } else {
+    CUDA_TRY(hlb_launch_state(h, h->f[h->cur], h->phase, h->t - 1, f, -1, h->stream));
+  } else if (h->scheme != HLB_AA) {
     // the spare population buffer is free until the next step
     void* spare = h->f[h->cur ^ 1];
-    CUDA_TRY(hlb_launch_state(h, h->f[h->cur], true, h->t - 1, spare, h->stream));
+    CUDA_TRY(hlb_launch_state(h, h->f[h->cur], h->phase, h->t - 1, spare, -1, h->stream));
     CUDA_TRY(cudaMemcpyAsync(f, spare, bytes, cudaMemcpyDeviceToHost, h->stream));
+  } else {
+    // one direction at a time through the read-back staging area
+    const size_t row = h->elem_bytes() * (size_t)h->n;
+    for (int i = 0; i < 19; ++i) {
+      CUDA_TRY(hlb_launch_state(h, h->f[0], h->phase, h->t - 1, h->d_stage, i, h->stream));
+      CUDA_TRY(cudaMemcpyAsync((char*)f + row * i, h->d_stage, row, cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   if (where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (t) *t = h->t;
@@ -477,7 +519,8 @@ extern "C" int hlb_set_state(hlb_solver* h, const void* f, int32_t where, int64_
                            where == HLB_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
   if (where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
   h->cur = 0;
-  h->phase = 0;
+  h->phase = HLB_READ_LOCAL;
   h->t = t;
+  h->stepped = false;
   return HLB_OK;
 }

@@ -1,11 +1,24 @@
 // hlb_forward.cu — forward kernels of the D3Q19 sparse-lattice solver.
 //
-// k_step: the fused stream-collide-boundary kernel (arXiv 2202.11770,
-//   Section 3.2.2: load f, compute rho and u (Eqs. 5-6), f^eq (Eq. 4),
-//   collide (Eq. 3a), stream (Eq. 3b) with wall and iolet boundaries, store).
-//   One thread per fluid site over the whole site list; the paper's six
-//   per-site-type kernels become one kernel in which boundary links are
-//   branch-free address selects (walls) plus a rare per-site fix-up (iolets).
+// The step (arXiv 2202.11770, Section 3.2.2: load f, compute rho and u
+// (Eqs. 5-6), f^eq (Eq. 4), collide (Eq. 3a), stream (Eq. 3b) with wall and
+// iolet boundaries, store) runs as one fused kernel per time step over the
+// whole site list; the paper's six per-site-type kernels become one kernel in
+// which wall links are branch-free address selects and iolet links a rare
+// per-site fix-up.  Two streaming schemes:
+//
+//  * pull A-B (k_step): read buffer A by gathering through the index table,
+//    write buffer B in place; 224 B per FP32 site update.
+//  * AA pattern (k_aa_even / k_aa_odd, then k_aa_fix over iolet sites): one
+//    buffer.  Even steps read a site's 19 slots and write them back swapped
+//    (no index table); odd steps read 19 slots through the index table and
+//    write the results to the very same 19 slots.  152 B (even) + 224 B
+//    (odd) per FP32 update.
+//
+// Read modes of the readback kernels: LOCAL (the buffer holds f(t) in place),
+// GATHER_AB (the buffer holds s'(t-1); boundaries applied while gathering),
+// GATHER_AA (AA buffer after an even step; boundaries already written).
+//
 // k_macros: the property cache of Section 3.2.2 step 7 (rho, u) plus WSS.
 // k_mass / k_flux / k_finish: FP64 reductions in a fixed order.
 #include <math.h>
@@ -21,9 +34,8 @@ constexpr int BLOCK = 256;
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
 // ---------------------------------------------------------------------------
-// Fused step.  GATHER = false: the buffer holds the pre-collision state f(t)
-// (right after initialisation or set_state); GATHER = true: it holds the
-// post-collision state s'(t-1) and f(t) is gathered from it.
+// Pull A-B step.  GATHER = false: the buffer holds the pre-collision state
+// f(t) (after initialisation or set_state); GATHER = true: it holds s'(t-1).
 // ---------------------------------------------------------------------------
 template <typename S, bool GATHER>
 __global__ void __launch_bounds__(BLOCK) k_step(const S* __restrict__ fin, S* __restrict__ fout,
@@ -46,22 +58,141 @@ __global__ void __launch_bounds__(BLOCK) k_step(const S* __restrict__ fin, S* __
   for (int i = 0; i < Q; ++i) stpop<S>(fout + (int64_t)i * n + x, h[i]);
 }
 
-template <typename S, bool GATHER>
+// ---------------------------------------------------------------------------
+// AA pattern.
+// ---------------------------------------------------------------------------
+// Address of slot i of site x in an odd step (and in an AA read-back): the
+// population arriving along c_i was written by the source x - c_i into its
+// opposite slot, or, for a non-fluid source, by x itself into slot i.
+__device__ __forceinline__ int64_t aa_addr(int i, int32_t s, int64_t n, int64_t x) {
+  return s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x;
+}
+
+// Even step: f(t) in place -> collide -> s'(t) stored swapped (slot ibar).
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_aa_even(S* A, const StepParams p) {
+  using R = typename Real<S>::type;
+  const int64_t n = p.n;
+  const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (x >= n) return;
+  R h[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) h[i] = to_real(A[(int64_t)i * n + x]);
+  collide<R>(h, R(p.omega));
+#pragma unroll
+  for (int i = 0; i < Q; ++i) stpop<S>(A + (int64_t)opp(i) * n + x, h[i]);
+}
+
+// Boundary value of iolet link (pull direction i, record L) at a site whose
+// pre-collision moments at time t are (drho, u) and whose outgoing
+// post-collision population is `out` (= s'_ibar): incoming f_i(t+1) - w_i.
+template <typename R>
+__device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, R ux, R uy, R uz,
+                                         const double* __restrict__ amp, const StepParams& p) {
+  const IoletParam io = p.io[L.iolet];
+  if (L.kind == 0) {
+    R r = p.ladd_rho_one ? R(1) : rho;
+    return out + R(L.coef) * r * R(amp[L.group]) * R(io.val);
+  }
+  R gx = ux, gy = uy, gz = uz;
+  if (!p.ghost_full_u) {
+    R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
+    gx = un * R(io.nx);
+    gy = un * R(io.ny);
+    gz = un * R(io.nz);
+  }
+  R drho = R(io.val);
+  R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
+  return heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
+}
+
+// After an AA step at time t: overwrite the slots that the iolet links of
+// each iolet site read in the next step with their boundary values, and
+// record the mass each link lets in.  One thread per iolet site.  The site's
+// stored post-collision populations s'_ibar(x) sit in slot i of x after an
+// even step, and in the slot it read direction i from after an odd step; an
+// iolet link's slot is slot i of x in both cases.  Boundary values use the
+// moments of these stored values, as the A-B gather does.
+template <typename S, bool ODD>
+__global__ void k_aa_fix(S* A, const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
+                         const double* __restrict__ amp, const int32_t* __restrict__ sites, int64_t nsites,
+                         const StepParams p, double* __restrict__ lflux) {
+  using R = typename Real<S>::type;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nsites) return;
+  const int64_t n = p.n;
+  const int64_t x = sites[q];
+  R v[Q];
+  v[0] = to_real(A[x]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i)
+    v[i] = to_real(A[ODD ? aa_addr(i, src[(int64_t)(i - 1) * n + x], n, x) : (int64_t)i * n + x]);
+  // v[k] = s'_kbar(x): rho = 1 + sum v, j = -sum v_k c_k
+  R d = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    d += v[k];
+    if (cx(k)) jx += cx(k) > 0 ? -v[k] : v[k];
+    if (cy(k)) jy += cy(k) > 0 ? -v[k] : v[k];
+    if (cz(k)) jz += cz(k) > 0 ? -v[k] : v[k];
+  }
+  const R rho = R(1) + d;
+  const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int32_t s = src[(int64_t)(i - 1) * n + x];
+    if (s > -2) continue;
+    const LinkRec L = links[-s - 2];
+    const R val = iolet_value<R>(i, L, v[i], rho, ux, uy, uz, amp, p);
+    lflux[-s - 2] = (double)val - (double)v[i];
+    A[(int64_t)i * n + x] = from_real<S>(val);
+  }
+}
+
+// Odd step: gather f(t) through the index table, collide, and write each
+// post-collision population into the slot it came from, where the site
+// downstream (or, across a wall or iolet, the site itself) reads it in the
+// next (even) step.  Iolet links get their boundary values from k_aa_fix.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
+  using R = typename Real<S>::type;
+  const int64_t n = p.n;
+  const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  if (x >= n) return;
+  R h[Q];
+  h[0] = to_real(A[x]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) h[i] = to_real(A[aa_addr(i, __ldg(src + (int64_t)(i - 1) * n + x), n, x)]);
+  collide<R>(h, R(p.omega));
+  stpop<S>(A + x, h[0]);
+  // The index table is read again for the store addresses rather than kept
+  // in registers across the collision: the same 72 bytes this thread has just
+  // read, served from L1/L2.
+#pragma unroll
+  for (int i = 1; i < Q; ++i) stpop<S>(A + aa_addr(i, __ldg(src + (int64_t)(i - 1) * n + x), n, x), h[opp(i)]);
+}
+
+// ---------------------------------------------------------------------------
+// Read-back kernels.
+// ---------------------------------------------------------------------------
+template <typename S, int MODE>
 __device__ __forceinline__ void load_state(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                            const LinkRec* __restrict__ links, const double* __restrict__ amp,
                                            const StepParams& p, int64_t x, typename Real<S>::type* h) {
-  if (GATHER) {
+  if (MODE == HLB_READ_GATHER_AB) {
     if (gather_site<S>(fin, src, p.n, x, h)) iolet_fixup<S>(fin, src, links, amp, p, x, h);
+  } else if (MODE == HLB_READ_GATHER_AA) {
+    h[0] = ldpop(fin + x);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) h[i] = ldpop(fin + aa_addr(i, src[(int64_t)(i - 1) * p.n + x], p.n, x));
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * p.n + x);
   }
 }
 
-// ---------------------------------------------------------------------------
 // Density, velocity and wall shear stress of f(t).
-// ---------------------------------------------------------------------------
-template <typename S, bool GATHER>
+template <typename S, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                   const LinkRec* __restrict__ links,
                                                   const double* __restrict__ amp,
@@ -73,7 +204,7 @@ __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, con
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (x >= n) return;
   R h[Q];
-  load_state<S, GATHER>(fin, src, links, amp, p, x, h);
+  load_state<S, MODE>(fin, src, links, amp, p, x, h);
   Macro<R> m = moments<R>(h);
   if (rho_out) rho_out[x] = (float)m.rho;
   if (u_out) {
@@ -129,17 +260,24 @@ __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, con
   wss_out[x] = (float)sqrt(tx * tx + ty * ty + tz * tz);
 }
 
-// Shifted pre-collision state f(t) - w into out [19][n].
-template <typename S, bool GATHER>
+// Shifted pre-collision state f(t) - w into out [19][n] (row < 0), or only
+// direction `row` into out [n].
+template <typename S, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_state(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                  const LinkRec* __restrict__ links,
                                                  const double* __restrict__ amp, const StepParams p,
-                                                 S* __restrict__ out) {
+                                                 S* __restrict__ out, int row) {
   using R = typename Real<S>::type;
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (x >= p.n) return;
   R h[Q];
-  load_state<S, GATHER>(fin, src, links, amp, p, x, h);
+  load_state<S, MODE>(fin, src, links, amp, p, x, h);
+  if (row >= 0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      if (i == row) out[x] = from_real<S>(h[i]);
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < Q; ++i) out[(int64_t)i * p.n + x] = from_real<S>(h[i]);
 }
@@ -180,7 +318,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // Per-block sums of drho (mass - n) into part[blockIdx.x].
-template <typename S, bool GATHER>
+template <typename S, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_mass(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                 const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const StepParams p,
@@ -191,7 +329,7 @@ __global__ void __launch_bounds__(BLOCK) k_mass(const S* __restrict__ fin, const
   double d = 0;
   if (x < p.n) {
     R h[Q];
-    load_state<S, GATHER>(fin, src, links, amp, p, x, h);
+    load_state<S, MODE>(fin, src, links, amp, p, x, h);
 #pragma unroll
     for (int i = 0; i < Q; ++i) d += (double)h[i];
   }
@@ -199,10 +337,10 @@ __global__ void __launch_bounds__(BLOCK) k_mass(const S* __restrict__ fin, const
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// Per-iolet flux: one block per iolet over its link records, in order.
+// Per-iolet flux of the A-B scheme: one block per iolet over its link
+// records, in order, recomputed from the post-collision state s'(t-1).
 template <typename S>
-__global__ void __launch_bounds__(BLOCK) k_flux(const S* __restrict__ fin, const int32_t* __restrict__ src,
-                                                const LinkRec* __restrict__ links,
+__global__ void __launch_bounds__(BLOCK) k_flux(const S* __restrict__ fin, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const StepParams p,
                                                 const int64_t* __restrict__ begin, double* __restrict__ out) {
   using R = typename Real<S>::type;
@@ -216,39 +354,30 @@ __global__ void __launch_bounds__(BLOCK) k_flux(const S* __restrict__ fin, const
     R own[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) own[i] = ldpop(fin + (int64_t)i * n + x);
+    const Macro<R> ms = moments<R>(own);
     const int j = L.dir;
-    // incoming boundary value minus the post-collision population leaving
-    // through the iolet (own[opp(j)]):
-    R contrib;
-    if (L.kind == 0) {
-      Macro<R> ms = moments<R>(own);
-      R rho = p.ladd_rho_one ? R(1) : ms.rho;
-      contrib = R(L.coef) * rho * R(amp[L.group]) * R(p.io[k].val);
-    } else {
-      Macro<R> ms = moments<R>(own);
-      R gx = ms.ux, gy = ms.uy, gz = ms.uz;
-      const IoletParam io = p.io[k];
-      if (!p.ghost_full_u) {
-        R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
-        gx = un * R(io.nx);
-        gy = un * R(io.ny);
-        gz = un * R(io.nz);
-      }
-      R drho = R(io.val);
-      R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
-      R hin = R(0);
-      // direction j is a runtime value: evaluate the equilibrium by a switch-free loop
+    R out = R(0);
 #pragma unroll
-      for (int i = 1; i < Q; ++i)
-        if (i == j) hin = heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
-      R hout = R(0);
+    for (int i = 1; i < Q; ++i)
+      if (i == opp(j)) out = own[i];
+    R val = R(0);
 #pragma unroll
-      for (int i = 1; i < Q; ++i)
-        if (i == opp(j)) hout = own[i];
-      contrib = hin - hout;
-    }
-    acc += (double)contrib;
+    for (int i = 1; i < Q; ++i)
+      if (i == j) val = iolet_value<R>(i, L, out, ms.rho, ms.ux, ms.uy, ms.uz, amp, p);
+    acc += (double)val - (double)out;
   }
+  double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[1 + k] = s;
+}
+
+// Per-iolet flux of the AA scheme: sum of the per-link values the last step
+// recorded, one block per iolet, in order.
+__global__ void __launch_bounds__(BLOCK) k_flux_sum(const double* __restrict__ lflux,
+                                                    const int64_t* __restrict__ begin, double* __restrict__ out) {
+  __shared__ double sh[BLOCK / 32];
+  const int k = blockIdx.x;
+  double acc = 0;
+  for (int64_t r = begin[k] + threadIdx.x; r < begin[k + 1]; r += BLOCK) acc += lflux[r];
   double s = block_sum(acc, sh);
   if (threadIdx.x == 0) out[1 + k] = s;
 }
@@ -276,7 +405,7 @@ __global__ void k_zero(double* p, int64_t m) {
 }
 
 // ---------------------------------------------------------------------------
-// dispatch helpers
+// dispatch
 // ---------------------------------------------------------------------------
 template <template <typename> class F, typename... A>
 cudaError_t dispatch(int precision, A... a) {
@@ -303,29 +432,52 @@ struct StepOp {
 };
 
 template <typename S>
+struct AAOp {
+  static cudaError_t run(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
+    StepParams p = h->params(t);
+    if (odd)
+      k_aa_odd<S><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
+    else
+      k_aa_even<S><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, p);
+    if (h->n_iolet_sites > 0) {
+      const unsigned g = (unsigned)((h->n_iolet_sites + 127) / 128);
+      if (odd)
+        k_aa_fix<S, true><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+                                            h->n_iolet_sites, p, h->d_lflux);
+      else
+        k_aa_fix<S, false><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+                                             h->n_iolet_sites, p, h->d_lflux);
+    }
+    return cudaGetLastError();
+  }
+};
+
+#define HLB_MODE_SWITCH(mode, KERNEL_LAUNCH)                  \
+  switch (mode) {                                              \
+    case HLB_READ_GATHER_AB: { constexpr int M = HLB_READ_GATHER_AB; KERNEL_LAUNCH; break; } \
+    case HLB_READ_GATHER_AA: { constexpr int M = HLB_READ_GATHER_AA; KERNEL_LAUNCH; break; } \
+    default: { constexpr int M = HLB_READ_LOCAL; KERNEL_LAUNCH; break; }                      \
+  }
+
+template <typename S>
 struct MacroOp {
-  static cudaError_t run(const hlb_solver* h, const void* fin, bool gather, int64_t tb, float* rho, float* u,
+  static cudaError_t run(const hlb_solver* h, const void* fin, int mode, int64_t tb, float* rho, float* u,
                          float* wss, cudaStream_t s) {
     StepParams p = h->params(tb);
     const float* nrm = h->has_normals ? h->d_normal : nullptr;
-    if (gather)
-      k_macros<S, true><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, nrm, p,
-                                                         rho, u, wss);
-    else
-      k_macros<S, false><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, nrm, p,
-                                                          rho, u, wss);
+    HLB_MODE_SWITCH(mode, (k_macros<S, M><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links,
+                                                                             h->d_amp, nrm, p, rho, u, wss)));
     return cudaGetLastError();
   }
 };
 
 template <typename S>
 struct StateOp {
-  static cudaError_t run(const hlb_solver* h, const void* fin, bool gather, int64_t tb, void* out, cudaStream_t s) {
+  static cudaError_t run(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
+                         cudaStream_t s) {
     StepParams p = h->params(tb);
-    if (gather)
-      k_state<S, true><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, (S*)out);
-    else
-      k_state<S, false><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, (S*)out);
+    HLB_MODE_SWITCH(mode, (k_state<S, M><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links,
+                                                                            h->d_amp, p, (S*)out, row)));
     return cudaGetLastError();
   }
 };
@@ -340,30 +492,30 @@ struct InitOp {
 
 template <typename S>
 struct ReduceOp {
-  static cudaError_t run(const hlb_solver* h, const void* fin, bool gather, int64_t tb, double* out,
+  static cudaError_t run(const hlb_solver* h, const void* fin, int mode, int64_t tb, bool have_flux, double* out,
                          cudaStream_t s) {
     StepParams p = h->params(tb);
     const int64_t nb = grid_for(h->n);
     double* part = h->d_red;
-    if (gather)
-      k_mass<S, true><<<(unsigned)nb, BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, part);
-    else
-      k_mass<S, false><<<(unsigned)nb, BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, part);
+    HLB_MODE_SWITCH(mode, (k_mass<S, M><<<(unsigned)nb, BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links,
+                                                                         h->d_amp, p, part)));
     k_finish<<<1, 1024, 0, s>>>(part, nb, h->n, out);
     if (h->n_iolets > 0) {
-      if (gather) {
-        const int64_t* begin = (const int64_t*)(h->d_red + nb);  // link ranges stored after the partials
-        k_flux<S><<<(unsigned)h->n_iolets, BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, begin,
-                                                          out);
-      } else {
+      const int64_t* begin = (const int64_t*)(h->d_red + nb);  // link ranges stored after the partials
+      if (!have_flux)
         k_zero<<<1, 256, 0, s>>>(out + 1, h->n_iolets);
-      }
+      else if (h->scheme == HLB_AA)
+        k_flux_sum<<<(unsigned)h->n_iolets, BLOCK, 0, s>>>(h->d_lflux, begin, out);
+      else
+        k_flux<S><<<(unsigned)h->n_iolets, BLOCK, 0, s>>>((const S*)fin, h->d_links, h->d_amp, p, begin, out);
     }
     return cudaGetLastError();
   }
 };
 
 }  // namespace
+
+int64_t hlb_reduce_partials(int64_t n) { return (int64_t)grid_for(n); }
 
 int64_t hlb_reduce_slots(int64_t n, int32_t n_iolets) {
   // per-block partials, iolet link ranges (int64, n_iolets + 1), final outputs (1 + n_iolets)
@@ -374,18 +526,21 @@ cudaError_t hlb_launch_step(const hlb_solver* h, const void* fin, void* fout, bo
                             cudaStream_t s) {
   return dispatch<StepOp>(h->precision, h, fin, fout, gather, tb, s);
 }
-cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, bool gather, int64_t tb, float* rho, float* u,
-                              float* wss, cudaStream_t s) {
-  return dispatch<MacroOp>(h->precision, h, fin, gather, tb, rho, u, wss, s);
+cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
+  return dispatch<AAOp>(h->precision, h, A, odd, t, s);
 }
-cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, bool gather, int64_t tb, void* out,
+cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, int mode, int64_t tb, float* rho, float* u,
+                              float* wss, cudaStream_t s) {
+  return dispatch<MacroOp>(h->precision, h, fin, mode, tb, rho, u, wss, s);
+}
+cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
                              cudaStream_t s) {
-  return dispatch<StateOp>(h->precision, h, fin, gather, tb, out, s);
+  return dispatch<StateOp>(h->precision, h, fin, mode, tb, out, row, s);
 }
 cudaError_t hlb_launch_init(const hlb_solver* h, void* f, double rho0, const float* u0, cudaStream_t s) {
   return dispatch<InitOp>(h->precision, h, f, rho0, u0, s);
 }
-cudaError_t hlb_launch_reduce(const hlb_solver* h, const void* fin, bool gather, int64_t tb, double* out_dev,
-                              cudaStream_t s) {
-  return dispatch<ReduceOp>(h->precision, h, fin, gather, tb, out_dev, s);
+cudaError_t hlb_launch_reduce(const hlb_solver* h, const void* fin, int mode, int64_t tb, bool have_flux,
+                              double* out_dev, cudaStream_t s) {
+  return dispatch<ReduceOp>(h->precision, h, fin, mode, tb, have_flux, out_dev, s);
 }

@@ -11,6 +11,9 @@
 #include "hemegb.h"
 #include "hlb_common.cuh"
 
+// How read-back kernels obtain f(t) from a population buffer.
+enum { HLB_READ_LOCAL = 0, HLB_READ_GATHER_AB = 1, HLB_READ_GATHER_AA = 2 };
+
 struct HostWave {
   int32_t kind = HLB_WAVE_CONST;
   double mean = 0, rel = 0, period = 1, phase = 0;
@@ -39,10 +42,11 @@ struct hlb_solver {
   // state
   cudaStream_t stream = nullptr;
   int device = 0;
-  void* f[2] = {nullptr, nullptr};    // population buffers [19][n] (storage precision)
+  void* f[2] = {nullptr, nullptr};    // population buffers [19][n] (storage precision); AA uses f[0]
   int cur = 0;                        // buffer holding the current state
-  int phase = 0;                      // 0: buffer holds f(t) (pre-collision); 1: holds s'(t-1)
+  int phase = 0;                      // HLB_READ_LOCAL: f(t) in place; GATHER_AB: s'(t-1); GATHER_AA: AA after an even step
   int64_t t = 0;
+  bool stepped = false;               // f(t) came from a step (iolet fluxes defined)
   double tau = 1.0;
   std::vector<HostWave> wave;         // per iolet
   std::vector<double> amp;            // per global group
@@ -54,6 +58,9 @@ struct hlb_solver {
   float* d_normal = nullptr;          // [3][n] or null
   float* d_stage = nullptr;           // [5][n] staging for host readback
   double* d_red = nullptr;            // reduction scratch
+  double* d_lflux = nullptr;          // [n_links] mass let in by each iolet link in the last AA step
+  int32_t* d_iolet_sites = nullptr;   // sites with at least one iolet link (AA boundary fix-up)
+  int64_t n_iolet_sites = 0;
   int64_t red_slots = 0;
 
   size_t elem_bytes() const;
@@ -67,18 +74,22 @@ int hlb_fail(int code, const std::string& msg);
 int hlb_cuda_fail(cudaError_t e, const char* where);
 
 // ---- launchers (hlb_forward.cu) ----
-// One time step from the current state (fin) into fout.
+// One pull A-B time step from fin into fout (gather: fin holds s'(t-1)).
 cudaError_t hlb_launch_step(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
                             cudaStream_t s);
+// One AA time step at time t on buffer A (odd: the buffer is in the swapped phase).
+cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s);
 // rho, u [3][n], wss of the current state, device outputs (any may be null).
-cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, bool gather, int64_t tb, float* rho,
-                              float* u, float* wss, cudaStream_t s);
-// Shifted pre-collision state into out [19][n] (storage precision).
-cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, bool gather, int64_t tb, void* out,
+cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, int mode, int64_t tb, float* rho, float* u,
+                              float* wss, cudaStream_t s);
+// Shifted pre-collision state into out [19][n] (row < 0) or direction `row` into out [n].
+cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
                              cudaStream_t s);
 // Equilibrium initialisation; u0 [3][n] device or null.
 cudaError_t hlb_launch_init(const hlb_solver* h, void* f, double rho0, const float* u0, cudaStream_t s);
-// Mass partial sums into d_red[0..nb), then the final sums; flux per iolet.
-cudaError_t hlb_launch_reduce(const hlb_solver* h, const void* fin, bool gather, int64_t tb, double* out_dev,
-                              cudaStream_t s);
+// Mass (out[0]) and per-iolet flux (out[1..]) in FP64.
+cudaError_t hlb_launch_reduce(const hlb_solver* h, const void* fin, int mode, int64_t tb, bool have_flux,
+                              double* out_dev, cudaStream_t s);
 int64_t hlb_reduce_slots(int64_t n, int32_t n_iolets);
+// Number of per-block mass partials at the start of the reduction scratch.
+int64_t hlb_reduce_partials(int64_t n);

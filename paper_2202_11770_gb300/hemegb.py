@@ -29,6 +29,7 @@ HLB_WAVE_CONST, HLB_WAVE_COSINE, HLB_WAVE_TABLE = 0, 1, 2
 HLB_HOST, HLB_DEVICE = 0, 1
 
 PRECISIONS = {"fp32": HLB_FP32, "bf16": HLB_BF16, "fp16": HLB_FP16, "fp64": HLB_FP64}
+SCHEMES = {"auto": HLB_SCHEME_AUTO, "ab": HLB_PULL_AB, "aa": HLB_AA}
 _ELEM = {HLB_FP32: 4, HLB_BF16: 2, HLB_FP16: 2, HLB_FP64: 8}
 
 
@@ -216,7 +217,7 @@ class Solver:
     object with ``xyz``, ``src``, ``iolets``, ``wall_normal``, ``amp_group``).
     """
 
-    def __init__(self, lattice, tau=1.0, precision="fp32", scheme=HLB_PULL_AB, ladd_rho_one=False,
+    def __init__(self, lattice, tau=1.0, precision="fp32", scheme="auto", ladd_rho_one=False,
                  ghost_full_u=False, use_normals=True, stream=None):
         torch = _torch()
         lib = library()
@@ -242,7 +243,8 @@ class Solver:
             amp_group=self._grp.ctypes.data_as(C.POINTER(C.c_int32)),
             n_iolets=len(self.iolets), iolets=ios)
         self._ios = ios
-        self._opt = hlb_options(precision=self.precision, scheme=int(scheme), ladd_rho_one=int(ladd_rho_one),
+        scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        self._opt = hlb_options(precision=self.precision, scheme=scheme, ladd_rho_one=int(ladd_rho_one),
                                 ghost_full_u=int(ghost_full_u))
         nbytes = hlb_workspace_bytes(self._lat, self._opt)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")

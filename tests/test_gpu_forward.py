@@ -19,12 +19,15 @@ pytestmark = pytest.mark.gpu
 hemegb = pytest.importorskip("paper_2202_11770_gb300.hemegb")
 
 
+SCHEMES = ["ab", "aa"]
+
+
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def _both(lat, tau, setup, precision="fp32", **kw):
-    s = hemegb.Solver(lat, tau=tau, precision=precision, **kw)
+def _both(lat, tau, setup, precision="fp32", scheme="ab", **kw):
+    s = hemegb.Solver(lat, tau=tau, precision=precision, scheme=scheme, **kw)
     o = oracle.Oracle(lat, tau=tau, ladd_rho_one=kw.get("ladd_rho_one", False),
                       ghost_full_u=kw.get("ghost_full_u", False))
     setup(s)
@@ -44,8 +47,9 @@ def pipe():
     return geo.pipe(8.0, 64)
 
 
-def test_pipe_fp32_1000_steps(pipe):
-    s, o = _both(pipe, 0.8, _pipe_bc)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_pipe_fp32_1000_steps(pipe, scheme):
+    s, o = _both(pipe, 0.8, _pipe_bc, scheme=scheme)
     s.step(1000)
     o.step(1000)
     rho, u, wss = s.macros()
@@ -62,11 +66,12 @@ def test_pipe_fp32_1000_steps(pipe):
     assert np.allclose(flux, o.flux(), rtol=1e-4, atol=1e-9)
 
 
-def test_pipe_fp64_matches_to_rounding(pipe):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_pipe_fp64_matches_to_rounding(pipe, scheme):
     def bc(x):
         x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.01, "rel": 0.5, "period": 60.0})
         x.set_pressure(1, {"kind": "cosine", "mean": 1.0, "rel": 0.001, "period": 45.0})
-    s, o = _both(pipe, 0.7, bc, precision="fp64")
+    s, o = _both(pipe, 0.7, bc, precision="fp64", scheme=scheme)
     s.step(300)
     o.step(300)
     f, t = s.state()
@@ -83,20 +88,22 @@ def test_pipe_fp64_matches_to_rounding(pipe):
     assert np.allclose(flux, o.flux(), rtol=1e-9, atol=1e-13)
 
 
+@pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16", "fp64"])
-def test_rest_state_exact(pipe, prec):
+def test_rest_state_exact(pipe, prec, scheme):
     def bc(x):
         x.set_velocity(0, [1.0], 0.0)
         x.set_pressure(1, 1.0)
-    s = hemegb.Solver(pipe, tau=0.8, precision=prec)
+    s = hemegb.Solver(pipe, tau=0.8, precision=prec, scheme=scheme)
     bc(s)
     s.init_equilibrium()
-    s.step(1000)
+    s.step(1001)
     f, _ = s.state()
     assert not f.view(np.uint8).any()         # shifted state stays exactly zero
 
 
-def test_streaming_permutation_bruteforce(d3q19):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_streaming_permutation_bruteforce(d3q19, scheme):
     c, w = d3q19
     from helpers import opposite_table
     opp = opposite_table(c)
@@ -108,7 +115,7 @@ def test_streaming_permutation_bruteforce(d3q19):
     rho0 = rng.uniform(0.9, 1.1, n)
     u0 = rng.uniform(-0.05, 0.05, (n, 3))
     f0 = np.stack([oracle.feq(rho0[k], u0[k]) for k in range(n)])     # equilibrium: collision is identity
-    s = hemegb.Solver(lat, tau=0.7, precision="fp64")
+    s = hemegb.Solver(lat, tau=0.7, precision="fp64", scheme=scheme)
     s.set_state((f0 - w).T.copy(), 0)
     s.step(1)          # collision is the identity on an equilibrium state
     got, t = s.state()  # gathered through the index table (post-collision buffer)
@@ -126,11 +133,12 @@ def test_streaming_permutation_bruteforce(d3q19):
     assert np.abs(got.T + w - exp).max() < 1e-14
 
 
-def test_isolated_site_and_small_lattices(d3q19):
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_isolated_site_and_small_lattices(d3q19, scheme):
     c, _ = d3q19
     for pts in ([(0, 0, 0)], [(0, 0, 0), (1, 0, 0)], [(0, 0, 0), (1, 1, 0), (1, 1, 1)]):
         lat = hand_lattice(pts, c)
-        s = hemegb.Solver(lat, tau=0.6, precision="fp32")
+        s = hemegb.Solver(lat, tau=0.6, precision="fp32", scheme=scheme)
         o = oracle.Oracle(lat, tau=0.6)
         rng = np.random.default_rng(len(pts))
         u0 = rng.uniform(-0.05, 0.05, (lat.n, 3))
@@ -144,7 +152,8 @@ def test_isolated_site_and_small_lattices(d3q19):
         assert np.abs(rho - rho_o).max() < 1e-6
 
 
-def test_tree_several_tiles_fp32():
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_tree_several_tiles_fp32(scheme):
     lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0)
     assert lat.n % 256
 
@@ -152,9 +161,9 @@ def test_tree_several_tiles_fp32():
         x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 200.0})
         for k in range(1, len(lat.iolets)):
             x.set_pressure(k, 1.0)
-    s, o = _both(lat, 0.55, bc)
-    s.step(300)
-    o.step(300)
+    s, o = _both(lat, 0.55, bc, scheme=scheme)
+    s.step(301)
+    o.step(301)
     _, u, wss = s.macros()
     _, u_o, wss_o = o.macros(lat.wall_normal)
     assert rel_l2(u, u_o) <= 1e-5
@@ -162,15 +171,16 @@ def test_tree_several_tiles_fp32():
     assert rel_l2(wss[wall], wss_o[wall]) < 1e-4
 
 
+@pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("opts", [dict(ladd_rho_one=True), dict(ghost_full_u=True)])
-def test_boundary_options(opts):
+def test_boundary_options(opts, scheme):
     lat = geo.tree(1, 5, root_radius=5.0, length_ratio=5.0)
 
     def bc(x):
         x.set_velocity(0, [1.0], 0.02)
         for k in range(1, len(lat.iolets)):
             x.set_pressure(k, 1.0 - 0.001 * k)
-    s, o = _both(lat, 0.6, bc, precision="fp64", **opts)
+    s, o = _both(lat, 0.6, bc, precision="fp64", scheme=scheme, **opts)
     s.step(100)
     o.step(100)
     _, u, _ = s.macros()
@@ -178,9 +188,10 @@ def test_boundary_options(opts):
     assert rel_l2(u, u_o) < 2e-7
 
 
-def test_mass_budget_and_closed_conservation():
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_mass_budget_and_closed_conservation(scheme):
     lat = geo.pipe(5.0, 20, geo.WALL, geo.WALL)
-    s = hemegb.Solver(lat, tau=0.6, precision="fp64")
+    s = hemegb.Solver(lat, tau=0.6, precision="fp64", scheme=scheme)
     rng = np.random.default_rng(5)
     s.init_equilibrium(1.0, rng.uniform(-0.02, 0.02, (3, lat.n)).astype(np.float32))
     m0, _ = s.reduce()
@@ -190,7 +201,7 @@ def test_mass_budget_and_closed_conservation():
 
     lat = geo.pipe(6.0, 24)
     for prec, tol in (("fp64", 1e-12), ("fp32", 1e-12)):
-        s = hemegb.Solver(lat, tau=0.7, precision=prec)
+        s = hemegb.Solver(lat, tau=0.7, precision=prec, scheme=scheme)
         s.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 40.0})
         s.set_pressure(1, {"kind": "cosine", "mean": 1.0, "rel": 0.002, "period": 25.0})
         s.init_equilibrium()
@@ -203,13 +214,14 @@ def test_mass_budget_and_closed_conservation():
             m = m1
 
 
-def test_state_roundtrip_resumes_bit_identical(pipe):
-    s, _ = _both(pipe, 0.8, _pipe_bc)
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_state_roundtrip_resumes_bit_identical(pipe, scheme):
+    s, _ = _both(pipe, 0.8, _pipe_bc, scheme=scheme)
     s.step(37)
     f, t = s.state()
     s.step(20)
     ref, _ = s.state()
-    s2 = hemegb.Solver(pipe, tau=0.8, precision="fp32")
+    s2 = hemegb.Solver(pipe, tau=0.8, precision="fp32", scheme=scheme)
     _pipe_bc(s2)
     s2.set_state(f, t)
     s2.step(20)
@@ -218,9 +230,10 @@ def test_state_roundtrip_resumes_bit_identical(pipe):
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
 
 
+@pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("prec,bound", [("bf16", 0.1), ("fp16", 0.02)])
-def test_16bit_storage_error_reported(pipe, prec, bound):
-    s, o = _both(pipe, 0.8, _pipe_bc, precision=prec)
+def test_16bit_storage_error_reported(pipe, prec, bound, scheme):
+    s, o = _both(pipe, 0.8, _pipe_bc, precision=prec, scheme=scheme)
     s.step(1000)
     o.step(1000)
     _, u, _ = s.macros()
@@ -244,15 +257,21 @@ def test_invalid_arguments(pipe):
     assert s.t == 0
 
 
-def test_full_size_tree_one_step_vs_oracle(d3q19):
+@pytest.fixture(scope="module")
+def tree20m():
+    return geo.tree(6, 2202, target_sites=20_000_000, length_ratio=5.0)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_full_size_tree_one_step_vs_oracle(d3q19, scheme, tree20m):
     """Seeded 20M-site depth-6 tree (the benchmark workload), FP32 solver in
     the benchmark's launch configuration: after 5 pulsatile steps, one more
     step is compared with the oracle's step from the same state, at every
     site; mass budget checked at full size."""
     _, w = d3q19
-    lat = geo.tree(6, 2202, target_sites=20_000_000, length_ratio=5.0)
+    lat = tree20m
     assert abs(lat.n - 20_000_000) < 0.02 * 20_000_000
-    s = hemegb.Solver(lat, tau=0.55, precision="fp32")
+    s = hemegb.Solver(lat, tau=0.55, precision="fp32", scheme=scheme)
     s.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 2000.0})
     for k in range(1, len(lat.iolets)):
         s.set_pressure(k, 1.0)
