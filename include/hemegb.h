@@ -220,6 +220,27 @@ int hlb_adjoint_run(hlb_solver* h, int64_t nsteps, const hlb_objective* obj, voi
                     size_t ws_bytes, double* J, double* dJ_dtau, double* dJ_damp);
 int hlb_n_amp_groups(const hlb_solver* h);
 
+/* Total mass without any allocation (the paper has no counterpart).  For
+ * callers that cannot allocate device memory where they need this number:
+ * a host framework whose allocator owns all device memory, or a
+ * time-critical loop where cudaMalloc's implicit synchronisation is not
+ * acceptable.  Sums a shifted population array f [19][n_sites] (device
+ * memory, storage `precision`, e.g. written by hlb_get_state with
+ * HLB_DEVICE) into *mass (one double in device memory) as
+ * n_sites + sum of all entries, in FP64, asynchronously on `stream`; the
+ * result equals hlb_reduce's mass of the same state.  Its per-block partial
+ * sums live in a fixed 2 MiB device array inside the library (one copy per
+ * GPU that loads the library, held until the process exits), so n_sites may
+ * not exceed HLB_STATIC_MAX_SITES: larger sizes return HLB_ERR_ARG.  The
+ * first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  Every
+ * call shares the array and leaves its partial sums there; nothing in it
+ * needs to start at zero.  Calls that overlap on the GPU (two streams, or two
+ * host threads) race on it and must be serialised by the caller.  No
+ * cudaMalloc, cudaFree or allocating library routine is called. */
+#define HLB_STATIC_MAX_SITES 67108864
+int hlb_mass_static(const void* f, int32_t precision, int64_t n_sites, double* mass, hlb_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,7 @@ _PROTOS = {
     "hlb_adjoint_workspace_bytes": (C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]),
     "hlb_adjoint_run": (C.c_int, [_P, C.c_int64, C.POINTER(hlb_objective), _P, C.c_size_t,
                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "hlb_mass_static": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P]),
 }
 
 _lib = None
