@@ -139,6 +139,19 @@ def set_bc(x, lat):
     workloads.apply_tree_bc(x, lat)
 
 
+def aggregate_ranks(ms_local, updates_local, dist=None, device="cpu"):
+    """Whole-job timing over replicas: the slowest rank's time and the sum of
+    all ranks' site updates (weak scaling; no data-path collective)."""
+    if dist is None:
+        return ms_local, updates_local
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(updates_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def time_form(lat, precision, scheme, steps, warmup, torch, dist=None):
     """Time `steps` launches with a CUDA event after each (solver stream).
 
@@ -275,6 +288,41 @@ def adjoint_ratio(steps, torch, sites=2_000_000):
     return out
 
 
+def precision_study(lat, checkpoints, torch):
+    """Velocity and wall-shear-stress error of FP32, BF16 and FP16 storage
+    against FP64 on the same lattice and boundary conditions, at the given
+    step counts.  The FP64 reference is the GPU FP64 path, which matches the
+    FP64 oracle to rounding in the parity tests (the oracle itself would need
+    hours for this size)."""
+    from paper_2202_11770_gb300 import hemegb
+    solvers = {}
+    for prec in ("fp64", "fp32", "bf16", "fp16"):
+        s = hemegb.Solver(lat, tau=0.55, precision=prec)
+        set_bc(s, lat)
+        s.init_equilibrium()
+        solvers[prec] = s
+    out = {}
+    done = 0
+    for k in checkpoints:
+        for s in solvers.values():
+            s.step(k - done)
+        done = k
+        ref = solvers["fp64"].macros_device()
+        wall = ~torch.isnan(ref[2])
+        row = {}
+        for prec in ("fp32", "bf16", "fp16"):
+            r, u, w = solvers[prec].macros_device()
+            row[prec] = {
+                "u_rel_l2": float(torch.linalg.norm(u - ref[1]) / torch.linalg.norm(ref[1])),
+                "wss_rel_l2": float(torch.linalg.norm(w[wall] - ref[2][wall]) / torch.linalg.norm(ref[2][wall])),
+                "rho_max_abs": float((r - ref[0]).abs().max()),
+            }
+        out[str(k)] = row
+    del solvers
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(lat, steps):
     import oracle
     o = oracle.Oracle(lat, tau=0.55)
@@ -339,11 +387,7 @@ def run_ours(args):
     clocks.start()
     ms, durs, t_first = time_form(lat, "fp32", scheme, args.steps, args.warmup, torch, dist)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_updates = n * args.steps * world
+    ms, total_updates = aggregate_ranks(ms, n * args.steps, dist, "cuda")
     value = total_updates / (ms * 1e-3) / 1e6
     head = form_stats(lat, "fp32", scheme, ms, durs, t_first, args.steps, peak)
     kname = "k_step" if scheme == "ab" else "k_aa_odd"
@@ -416,6 +460,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-sites", type=int, default=2_000_000)
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint/forward timing")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="u and WSS error of FP32/BF16/FP16 storage vs FP64 at 1k, 5k, 10k steps")
     ap.add_argument("--ref-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="FP32 only, no e2e (profiling runs)")
@@ -426,6 +472,14 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.precision_study:
+        import torch
+        torch.cuda.set_device(0)
+        lat = tree_lattice(args.sites)
+        res = precision_study(lat, [1000, 5000, 10000], torch)
+        print(json.dumps({"precision_study": res, "n_sites": lat.n, "workload": WORKLOAD,
+                          "reference": "GPU FP64 storage and arithmetic (equal to the FP64 oracle to rounding "
+                                       "in the parity tests)"}))
     elif args.adjoint_only:
         import torch
         torch.cuda.set_device(0)

@@ -30,6 +30,31 @@ namespace {
 constexpr int BLOCK = 256;
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
+// Probe sites as a bit mask over sites plus per-32-site prefix counts: site
+// x is a probe when bit x of mask is set, and its target is
+// target[base[x / 32] + popcount(mask bits of its word below x)].  Lets the
+// reverse kernels add dJ/df(t) at the probes without a separate launch.
+struct ProbeMap {
+  const uint32_t* mask;
+  const int32_t* base;
+  const double* target;  // ordered by site
+  double ax, ay, az;
+  double g2;             // 2 / N
+};
+
+// dJ/df_j(t) at site x = pg (c_j . axis - u_ax); pg = 0 off the probes.
+template <typename R>
+__device__ __forceinline__ R probe_coef(const ProbeMap& pm, int64_t x, const Macro<R>& m, R* uax) {
+  const uint32_t word = pm.mask[x >> 5];
+  const uint32_t bit = (uint32_t)(x & 31);
+  *uax = R(0);
+  if (!((word >> bit) & 1u)) return R(0);
+  const int k = pm.base[x >> 5] + __popc(word & ((1u << bit) - 1u));
+  const R ua = m.ux * R(pm.ax) + m.uy * R(pm.ay) + m.uz * R(pm.az);
+  *uax = ua;
+  return R(pm.g2) * (ua - R(pm.target[k])) / m.rho;
+}
+
 struct AdjParams {
   StepParams prev;            // boundary data of G_{t-1} (recomputing f(t))
   double val_cur[MAX_IOLETS];  // waveform values of G_t (velocity w, pressure rho - 1)
@@ -48,165 +73,219 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// Adjoint of one reverse step at site x (GPREV: f(t) is gathered from
-// s'(t-1); false only at t = 0 where prev holds f(0) itself).  With
-// IOLET = false the site is skipped (returns false) when it has an iolet
-// link; those sites go through the IOLET = true instantiation, which adds
-// the boundary transposes.  Returns the site's dJ/dtau contribution in *dtau.
-template <typename S, bool GPREV, bool IOLET>
-__device__ __forceinline__ bool adjoint_site(const S* __restrict__ prev, const S* __restrict__ cur,
-                                             const S* __restrict__ mu_next, S* __restrict__ mu_out,
-                                             const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
-                                             const double* __restrict__ amp, const AdjParams& ap,
-                                             double* __restrict__ dlink, int store, int64_t x, double* dtau) {
+// Bulk reverse step over all sites without iolet links: a persistent tile
+// loop whose staged index tile serves both gathers.  f(t) is gathered from
+// s'(t-1) first; its moments are kept and its non-equilibrium parts
+// h_i - heq_i are parked in shared memory, so that the 19 gathered values of
+// mu(t+1) can reuse the registers (keeping both 19-vectors live would halve
+// the resident warps).  Then lam = G_t^T mu(t+1) and
+// mu_j(t) = (1 - omega) lam_j + omega (S0 + (c_j - u).B).
+template <typename S, bool GPREV>
+__global__ void __launch_bounds__(TILE, sizeof(typename Real<S>::type) == 8 ? 1 : 3) k_adjoint(const S* __restrict__ prev, const S* __restrict__ mu_next,
+                                                  S* __restrict__ mu_out, const int32_t* __restrict__ src,
+                                                  const AdjParams ap, const ProbeMap pm, double* __restrict__ dtau_part,
+                                                  int store, int* err) {
   using R = typename Real<S>::type;
-  const StepParams& p = ap.prev;
-  const int64_t n = p.n;
-  R h[Q], lam[Q];
-  bool any_iolet = false;
-  h[0] = ldpop(prev + x);
-  lam[0] = ldpop(mu_next + x);
+  __shared__ IdxTiles t;
+  __shared__ R neq[Q][TILE];
+  __shared__ double sh[TILE / 32];
+  const int64_t n = ap.prev.n;
+  const R omega = R(ap.prev.omega);
+  double dtau_local = 0;
+  tile_loop(t, src, n, ap.prev.sn, err, [&](int64_t x, const int32_t* codes, bool ok) {
+    if (!ok || x >= n) return;
+    bool iolet = false;
+    Macro<R> m;
+    {
+      R h[Q];
+      h[0] = ldpop(prev + x);
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int32_t s = ldidx(src + (int64_t)(i - 1) * n + x);
-    if (GPREV) h[i] = ldpop(prev + (s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x));
-    else h[i] = ldpop(prev + (int64_t)i * n + x);
-    // s'_opp(i)(x) is read by x - c_i = x + c_opp(i) in direction opp(i),
-    // or by x itself in direction i when that source is not fluid
-    lam[opp(i)] = ldpop(mu_next + (s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x));
-    any_iolet |= s <= -2;
-  }
-  if (!IOLET && any_iolet) return false;
-  if (IOLET) {
-    if (GPREV) iolet_fixup<S>(prev, src, links, amp, p, x, h);
-    // boundary terms of G_t, which reads the moments of s'(t) at x
-    R d = R(0), jx = R(0), jy = R(0), jz = R(0);
+      for (int i = 1; i < Q; ++i) {
+        const int32_t s = codes[(i - 1) * TILE];
+        h[i] = ldpop(prev + (GPREV ? (s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x) : (int64_t)i * n + x));
+        iolet |= s <= -2;
+      }
+      if (iolet) return;  // k_adjoint_iolet
+      m = moments<R>(h);
+      const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      R v = ldpop(cur + (int64_t)i * n + x);
-      d += v;
-      if (cx(i)) jx += cx(i) > 0 ? v : -v;
-      if (cy(i)) jy += cy(i) > 0 ? v : -v;
-      if (cz(i)) jz += cz(i) > 0 ? v : -v;
+      for (int i = 0; i < Q; ++i) neq[i][threadIdx.x] = h[i] - heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15);
     }
-    const R rho_s = R(1) + d;
-    const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
-    R gsum = R(0), gux = R(0), guy = R(0), guz = R(0);
+    R lam[Q];
+    lam[0] = ldpop(mu_next + x);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int32_t s = src[(int64_t)(i - 1) * n + x];
-      if (s > -2) continue;
-      const int64_t r = -s - 2;
+      const int32_t s = codes[(i - 1) * TILE];
+      // s'_opp(i)(x) is read by x - c_i = x + c_opp(i) in direction opp(i)
+      lam[opp(i)] = ldpop(mu_next + (s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x));
+    }
+    const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    R S0 = R(0), Lw = R(0), Bx = R(0), By = R(0), Bz = R(0), dt = R(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const R cu = cdotu<R>(i, m.ux, m.uy, m.uz);
+      const R w = wgt<R>(i);
+      S0 += lam[i] * w * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15);  // feq_i / rho
+      Lw += lam[i] * w;
+      const R b = lam[i] * w * (R(3) + R(9) * cu);
+      if (cx(i)) Bx += cx(i) > 0 ? b : -b;
+      if (cy(i)) By += cy(i) > 0 ? b : -b;
+      if (cz(i)) Bz += cz(i) > 0 ? b : -b;
+      dt += lam[i] * neq[i][threadIdx.x];
+    }
+    Bx -= R(3) * m.ux * Lw;
+    By -= R(3) * m.uy * Lw;
+    Bz -= R(3) * m.uz * Lw;
+    dtau_local += (double)(omega * omega * dt);
+    if (store) {
+      // mu_j = (1-omega) lam_j + omega (S0 + (c_j - u).B) + pg (c_j - u).axis
+      //      = (1-omega) lam_j + T0 + c_j.E
+      R uax;
+      const R pg = probe_coef<R>(pm, x, m, &uax);
+      const R Ex = omega * Bx + pg * R(pm.ax), Ey = omega * By + pg * R(pm.ay), Ez = omega * Bz + pg * R(pm.az);
+      const R T0 = omega * (S0 - m.ux * Bx - m.uy * By - m.uz * Bz) - pg * uax;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        R v = (R(1) - omega) * lam[j] + T0;
+        if (cx(j)) v += cx(j) > 0 ? Ex : -Ex;
+        if (cy(j)) v += cy(j) > 0 ? Ey : -Ey;
+        if (cz(j)) v += cz(j) > 0 ? Ez : -Ez;
+        mu_out[(int64_t)j * n + x] = from_real<S>(v);
+      }
+    }
+  });
+  const double bs = block_sum(dtau_local, sh);
+  if (threadIdx.x == 0) dtau_part[blockIdx.x] += bs;
+}
+
+// Reverse step of the sites with iolet links: one warp per site, lane i =
+// direction i.  Recomputes f(t) with the boundary values of G_{t-1} (as the
+// forward computed them), forms lam = G_t^T mu(t+1) including the transposes
+// of the Ladd and ghost-density boundaries of G_t (which read the moments of
+// s'(t) at the site), applies the collision transpose, and accumulates the
+// per-link amplitude derivatives (each link record belongs to one lane).
+template <typename S, bool GPREV>
+__global__ void __launch_bounds__(256) k_adjoint_iolet(const S* __restrict__ prev, const S* __restrict__ cur,
+                                                       const S* __restrict__ mu_next, S* __restrict__ mu_out,
+                                                       const int32_t* __restrict__ src,
+                                                       const LinkRec* __restrict__ links,
+                                                       const double* __restrict__ amp, const AdjParams ap,
+                                                       const ProbeMap pm, const int32_t* __restrict__ sites,
+                                                       int64_t nsites, double* __restrict__ dtau_part,
+                                                       double* __restrict__ dlink, int store) {
+  using R = typename Real<S>::type;
+  __shared__ double sh[8];
+  const StepParams& p = ap.prev;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int i = threadIdx.x & 31;
+  const bool dir = i < Q;
+  double dtau_local = 0;
+  if (w < nsites) {  // uniform across the warp
+    const int64_t n = p.n, x = sites[w];
+    const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
+    // f(t) at x: gathered from s'(t-1) with the boundary values of G_{t-1}
+    R h = R(0);
+    if (GPREV) {
+      R own = R(0);
+      if (dir) {
+        h = ldpop(prev + (i == 0 ? x : (code >= 0 ? (int64_t)i * n + code : (int64_t)lane_opp(i) * n + x)));
+        own = ldpop(prev + (int64_t)i * n + x);
+      }
+      R d, jx, jy, jz;
+      lane_moment_sums<R>(own, R(1), &d, &jx, &jy, &jz);
+      const R rp = R(1) + d;
+      const R ux = jx / rp, uy = jy / rp, uz = jz / rp;
+      if (code <= -2) {
+        const LinkRec L = links[-code - 2];
+        const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+        h = lane_iolet_value<R>(i, L, h, rp, ux, uy, uz, a, p);
+      }
+    } else if (dir) {
+      h = ldpop(prev + (int64_t)i * n + x);
+    }
+    // lane i loads lam_opp(i): s'_opp(i)(x) is read by x - c_i in direction
+    // opp(i), or by x itself in direction i across a boundary
+    R lo = R(0);
+    if (dir) lo = ldpop(mu_next + (i == 0 ? x : (code >= 0 ? (int64_t)lane_opp(i) * n + code : (int64_t)i * n + x)));
+    // boundary transposes of G_t (moments of s'(t) at x)
+    const R c = dir ? ldpop(cur + (int64_t)i * n + x) : R(0);
+    R d, jx, jy, jz;
+    lane_moment_sums<R>(c, R(1), &d, &jx, &jy, &jz);
+    const R rho_s = R(1) + d;
+    const R usx = jx / rho_s, usy = jy / rho_s, usz = jz / rho_s;
+    R gs = R(0), gx = R(0), gy = R(0), gz = R(0);
+    if (code <= -2) {
+      const int64_t r = -code - 2;
       const LinkRec L = links[r];
       const R a = ldpop(mu_next + (int64_t)i * n + x);  // adjoint of f_i(x, t+1)
       const R val = R(ap.val_cur[L.iolet]);
       if (L.kind == 0) {
         const R rho = p.ladd_rho_one ? R(1) : rho_s;
-        if (!p.ladd_rho_one) gsum += a * R(L.coef) * R(amp[L.group]) * val;
+        if (!p.ladd_rho_one) gs = a * R(L.coef) * R(amp[L.group]) * val;
         dlink[r] += (double)(a * R(L.coef) * rho * val);
       } else {
-        lam[opp(i)] = R(0);  // the ghost value does not read s'_opp(i)(x)
+        lo = R(0);  // the ghost value does not read s'_opp(i)(x)
         const IoletParam io = p.io[L.iolet];
-        R gx = ux, gy = uy, gz = uz;
+        R ex = usx, ey = usy, ez = usz;
         if (!p.ghost_full_u) {
-          const R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
-          gx = un * R(io.nx);
-          gy = un * R(io.ny);
-          gz = un * R(io.nz);
+          const R un = ex * R(io.nx) + ey * R(io.ny) + ez * R(io.nz);
+          ex = un * R(io.nx);
+          ey = un * R(io.ny);
+          ez = un * R(io.nz);
         }
         const R rho_k = R(1) + val;
-        const R cu = cdotu<R>(i, gx, gy, gz);
-        const R k3 = a * wgt<R>(i) * rho_k;
+        const R cu = lane_cdotu<R>(i, ex, ey, ez);
+        const R k3 = a * lane_w<R>(i) * rho_k;
         // d f^eq_i / d u_g = w_i rho_k (3 c_i + 9 (c_i . u_g) c_i - 3 u_g)
-        R vx = k3 * (R(3) * cx(i) + R(9) * cu * cx(i) - R(3) * gx);
-        R vy = k3 * (R(3) * cy(i) + R(9) * cu * cy(i) - R(3) * gy);
-        R vz = k3 * (R(3) * cz(i) + R(9) * cu * cz(i) - R(3) * gz);
+        R vx = k3 * (R(3) * k_cx[i] + R(9) * cu * k_cx[i] - R(3) * ex);
+        R vy = k3 * (R(3) * k_cy[i] + R(9) * cu * k_cy[i] - R(3) * ey);
+        R vz = k3 * (R(3) * k_cz[i] + R(9) * cu * k_cz[i] - R(3) * ez);
         if (!p.ghost_full_u) {
           const R vn = vx * R(io.nx) + vy * R(io.ny) + vz * R(io.nz);
           vx = vn * R(io.nx);
           vy = vn * R(io.ny);
           vz = vn * R(io.nz);
         }
-        gux += vx;
-        guy += vy;
-        guz += vz;
+        gx = vx;
+        gy = vy;
+        gz = vz;
       }
     }
-    // d u_s / d s'_j = (c_j - u_s) / rho_s;  d rho_s / d s'_j = 1
-#pragma unroll
-    for (int j = 0; j < Q; ++j)
-      lam[j] += gsum + ((R(cx(j)) - ux) * gux + (R(cy(j)) - uy) * guy + (R(cz(j)) - uz) * guz) / rho_s;
-  }
-  // collision adjoint at f(t) = h
-  const Macro<R> m = moments<R>(h);
-  const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-  const R omega = R(p.omega);
-  R S0 = R(0), Lw = R(0), Bx = R(0), By = R(0), Bz = R(0), dt = R(0);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const R cu = cdotu<R>(i, m.ux, m.uy, m.uz);
-    const R w = wgt<R>(i);
-    S0 += lam[i] * w * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15);  // feq_i / rho
-    Lw += lam[i] * w;
-    const R b = lam[i] * w * (R(3) + R(9) * cu);
-    if (cx(i)) Bx += cx(i) > 0 ? b : -b;
-    if (cy(i)) By += cy(i) > 0 ? b : -b;
-    if (cz(i)) Bz += cz(i) > 0 ? b : -b;
-    dt += lam[i] * (h[i] - heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15));
-  }
-  // (1/rho) d feq_i/d u_a summed with lam: B_a - 3 u_a Lw
-  Bx -= R(3) * m.ux * Lw;
-  By -= R(3) * m.uy * Lw;
-  Bz -= R(3) * m.uz * Lw;
-  *dtau = (double)(omega * omega * dt);
-  if (store) {
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      const R v = (R(1) - omega) * lam[j] +
-                  omega * (S0 + (R(cx(j)) - m.ux) * Bx + (R(cy(j)) - m.uy) * By + (R(cz(j)) - m.uz) * Bz);
-      mu_out[(int64_t)j * n + x] = from_real<S>(v);
+    const R gsum = lane_sum<R>(gs), gux = lane_sum<R>(gx), guy = lane_sum<R>(gy), guz = lane_sum<R>(gz);
+    // lam_i, with d u_s / d s'_j = (c_j - u_s) / rho_s and d rho_s / d s'_j = 1
+    R lam = __shfl_sync(FULL_MASK, lo, lane_opp(i < Q ? i : 0));
+    lam += gsum + ((R(k_cx[i]) - usx) * gux + (R(k_cy[i]) - usy) * guy + (R(k_cz[i]) - usz) * guz) / rho_s;
+    if (!dir) lam = R(0);
+    // collision transpose at f(t) = h
+    const Macro<R> m = lane_moments<R>(h);
+    const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    const R omega = R(p.omega);
+    const R cu = lane_cdotu<R>(i, m.ux, m.uy, m.uz);
+    const R wi = lane_w<R>(i);
+    const R b = lam * wi * (R(3) + R(9) * cu);
+    const R S0 = lane_sum<R>(lam * wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15));
+    const R Lw = lane_sum<R>(lam * wi);
+    R Bx = lane_sum<R>(b * R(k_cx[i])), By = lane_sum<R>(b * R(k_cy[i])), Bz = lane_sum<R>(b * R(k_cz[i]));
+    const R dt = lane_sum<R>(dir ? lam * (h - lane_heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15)) : R(0));
+    Bx -= R(3) * m.ux * Lw;
+    By -= R(3) * m.uy * Lw;
+    Bz -= R(3) * m.uz * Lw;
+    if (i == 0) dtau_local = (double)(omega * omega * dt);
+    if (store && dir) {
+      R uax;
+      const R pg = probe_coef<R>(pm, x, m, &uax);
+      R v = (R(1) - omega) * lam +
+            omega * (S0 + (R(k_cx[i]) - m.ux) * Bx + (R(k_cy[i]) - m.uy) * By + (R(k_cz[i]) - m.uz) * Bz);
+      v += pg * (R(k_cx[i]) * R(pm.ax) + R(k_cy[i]) * R(pm.ay) + R(k_cz[i]) * R(pm.az) - uax);
+      mu_out[(int64_t)i * n + x] = from_real<S>(v);
     }
   }
-  return true;
-}
-
-// Bulk reverse step over all sites without iolet links.
-template <typename S, bool GPREV>
-__global__ void __launch_bounds__(BLOCK) k_adjoint(const S* __restrict__ prev, const S* __restrict__ mu_next,
-                                                   S* __restrict__ mu_out, const int32_t* __restrict__ src,
-                                                   const AdjParams ap, double* __restrict__ dtau_part, int store) {
-  __shared__ double sh[BLOCK / 32];
-  const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-  double dtau_local = 0;
-  if (x < ap.prev.n)
-    adjoint_site<S, GPREV, false>(prev, nullptr, mu_next, mu_out, src, nullptr, nullptr, ap, nullptr, store, x,
-                                  &dtau_local);
-  const double bs = block_sum(dtau_local, sh);
-  if (threadIdx.x == 0) dtau_part[blockIdx.x] += bs;
-}
-
-// Reverse step of the sites with iolet links (one thread per site).
-template <typename S, bool GPREV>
-__global__ void __launch_bounds__(128) k_adjoint_iolet(const S* __restrict__ prev, const S* __restrict__ cur,
-                                                       const S* __restrict__ mu_next, S* __restrict__ mu_out,
-                                                       const int32_t* __restrict__ src,
-                                                       const LinkRec* __restrict__ links,
-                                                       const double* __restrict__ amp, const AdjParams ap,
-                                                       const int32_t* __restrict__ sites, int64_t nsites,
-                                                       double* __restrict__ dtau_part, double* __restrict__ dlink,
-                                                       int store) {
-  __shared__ double sh[4];
-  const int64_t q = (int64_t)blockIdx.x * 128 + threadIdx.x;
-  double dtau_local = 0;
-  if (q < nsites)
-    adjoint_site<S, GPREV, true>(prev, cur, mu_next, mu_out, src, links, amp, ap, dlink, store, sites[q],
-                                 &dtau_local);
   const double bs = block_sum(dtau_local, sh);
   if (threadIdx.x == 0) dtau_part[blockIdx.x] += bs;
 }
 
 // Objective term at time t for every probe: accumulate (u.axis - target)^2 / N.
-template <typename S, bool GATHER>
+template <typename S, int MODE>
 __global__ void k_probe_obj(const S* __restrict__ fin, const int32_t* __restrict__ src,
                             const LinkRec* __restrict__ links, const double* __restrict__ amp, const StepParams p,
                             const int64_t* __restrict__ sites, const double* __restrict__ target, double ax,
@@ -216,12 +295,7 @@ __global__ void k_probe_obj(const S* __restrict__ fin, const int32_t* __restrict
   if (q >= np) return;
   const int64_t x = sites[q];
   R h[Q];
-  if (GATHER) {
-    if (gather_site<S>(fin, src, p.n, x, h)) iolet_fixup<S>(fin, src, links, amp, p, x, h);
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * p.n + x);
-  }
+  load_state<S, MODE>(fin, src, links, amp, p, x, h);
   const Macro<R> m = moments<R>(h);
   const double ua = (double)m.ux * ax + (double)m.uy * ay + (double)m.uz * az;
   const double d = ua - target[q];
@@ -230,7 +304,7 @@ __global__ void k_probe_obj(const S* __restrict__ fin, const int32_t* __restrict
 
 // Objective derivative at time t added to mu(t) at the probes:
 // dJ/df_j = (2/N) (u.axis - target) (c_j.axis - u.axis) / rho.
-template <typename S, bool GATHER>
+template <typename S, int MODE>
 __global__ void k_probe_adj(const S* __restrict__ fin, const int32_t* __restrict__ src,
                             const LinkRec* __restrict__ links, const double* __restrict__ amp, const StepParams p,
                             const int64_t* __restrict__ sites, const double* __restrict__ target, double ax,
@@ -240,12 +314,7 @@ __global__ void k_probe_adj(const S* __restrict__ fin, const int32_t* __restrict
   if (q >= np) return;
   const int64_t x = sites[q];
   R h[Q];
-  if (GATHER) {
-    if (gather_site<S>(fin, src, p.n, x, h)) iolet_fixup<S>(fin, src, links, amp, p, x, h);
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * p.n + x);
-  }
+  load_state<S, MODE>(fin, src, links, amp, p, x, h);
   const Macro<R> m = moments<R>(h);
   const R ua = m.ux * R(ax) + m.uy * R(ay) + m.uz * R(az);
   const R g = R(2.0 * invN) * (ua - R(target[q])) / m.rho;
@@ -275,35 +344,51 @@ __global__ void k_adj_finish(const double* __restrict__ jp, int64_t np, const do
   (void)ngroups;
 }
 
-__global__ void k_fill(double* p, int64_t m) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) p[i] = 0;
+
+// Persistent grid of the bulk reverse kernel (resident CTAs x SMs, capped by
+// the tile count); its per-CTA partials occupy the first slots of dtau_part.
+template <typename K>
+unsigned adj_grid(const hlb_solver* h, K kernel) {
+  static int cache[64] = {0};
+  const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
+  if (!cache[dev]) {
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // prefer the largest shared-memory carveout: these kernels stage index tiles
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TILE, 0);
+    cache[dev] = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
+  }
+  const int64_t ntiles = (h->n + TILE - 1) / TILE;
+  return (unsigned)(ntiles < cache[dev] ? ntiles : cache[dev]);
 }
 
 template <typename S>
 cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, const void* cur, const void* mu_next,
-                           void* mu_out, int64_t tb_prev, int64_t tb_cur, double* dtau_part, double* dlink,
-                           bool store, cudaStream_t st) {
+                           void* mu_out, int64_t tb_prev, int64_t tb_cur, const ProbeMap& pm, double* dtau_part,
+                           double* dlink, bool store, cudaStream_t st) {
   AdjParams ap;
   ap.prev = h->params(tb_prev);
   StepParams pc = h->params(tb_cur);
   for (int k = 0; k < MAX_IOLETS; ++k) ap.val_cur[k] = k < h->n_iolets ? pc.io[k].val : 0.0;
   const int st_ = store ? 1 : 0;
   double* part_i = dtau_part + grid_for(h->n);  // partials of the iolet-site kernel
-  const unsigned gi = (unsigned)((h->n_iolet_sites + 127) / 128);
+  const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // one warp per iolet site
   if (gprev) {
-    k_adjoint<S, true><<<grid_for(h->n), BLOCK, 0, st>>>((const S*)prev, (const S*)mu_next, (S*)mu_out, h->d_src, ap,
-                                                         dtau_part, st_);
+    k_adjoint<S, true><<<adj_grid(h, k_adjoint<S, true>), TILE, 0, st>>>((const S*)prev, (const S*)mu_next,
+                                                                          (S*)mu_out, h->d_src, ap, pm, dtau_part,
+                                                                          st_, h->d_err);
     if (gi)
-      k_adjoint_iolet<S, true><<<gi, 128, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
-                                                   h->d_src, h->d_links, h->d_amp, ap, h->d_iolet_sites,
+      k_adjoint_iolet<S, true><<<gi, 256, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
+                                                   h->d_src, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
                                                    h->n_iolet_sites, part_i, dlink, st_);
   } else {
-    k_adjoint<S, false><<<grid_for(h->n), BLOCK, 0, st>>>((const S*)prev, (const S*)mu_next, (S*)mu_out, h->d_src, ap,
-                                                          dtau_part, st_);
+    k_adjoint<S, false><<<adj_grid(h, k_adjoint<S, false>), TILE, 0, st>>>((const S*)prev, (const S*)mu_next,
+                                                                            (S*)mu_out, h->d_src, ap, pm, dtau_part,
+                                                                            st_, h->d_err);
     if (gi)
-      k_adjoint_iolet<S, false><<<gi, 128, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
-                                                    h->d_src, h->d_links, h->d_amp, ap, h->d_iolet_sites,
+      k_adjoint_iolet<S, false><<<gi, 256, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
+                                                    h->d_src, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
                                                     h->n_iolet_sites, part_i, dlink, st_);
   }
   return cudaGetLastError();
@@ -316,47 +401,51 @@ struct Probe {
   int64_t np;
 };
 
+#define PROBE_MODE_SWITCH(mode, LAUNCH)                                    \
+  switch (mode) {                                                         \
+    case 1: { constexpr int M = 1; LAUNCH; break; }                       \
+    case 2: { constexpr int M = 2; LAUNCH; break; }                       \
+    default: { constexpr int M = 0; LAUNCH; break; }                      \
+  }
+
 template <typename S>
-cudaError_t launch_probe_obj(const hlb_solver* h, const void* fin, bool gather, int64_t tb, const Probe& pr, double* jp,
+cudaError_t launch_probe_obj(const hlb_solver* h, const void* fin, int mode, int64_t tb, const Probe& pr, double* jp,
                              cudaStream_t st) {
   if (pr.np == 0) return cudaSuccess;
   StepParams p = h->params(tb);
   const unsigned g = (unsigned)((pr.np + 127) / 128);
-  if (gather)
-    k_probe_obj<S, true><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, pr.sites, pr.target,
-                                            pr.ax, pr.ay, pr.az, pr.invN, pr.np, jp);
-  else
-    k_probe_obj<S, false><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, pr.sites, pr.target,
-                                             pr.ax, pr.ay, pr.az, pr.invN, pr.np, jp);
+  PROBE_MODE_SWITCH(mode, (k_probe_obj<S, M><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p,
+                                                                 pr.sites, pr.target, pr.ax, pr.ay, pr.az, pr.invN,
+                                                                 pr.np, jp)));
   return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_probe_adj(const hlb_solver* h, const void* fin, bool gather, int64_t tb, const Probe& pr, void* mu,
+cudaError_t launch_probe_adj(const hlb_solver* h, const void* fin, int mode, int64_t tb, const Probe& pr, void* mu,
                              cudaStream_t st) {
   if (pr.np == 0) return cudaSuccess;
   StepParams p = h->params(tb);
   const unsigned g = (unsigned)((pr.np + 127) / 128);
-  if (gather)
-    k_probe_adj<S, true><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, pr.sites, pr.target,
-                                            pr.ax, pr.ay, pr.az, pr.invN, pr.np, (S*)mu);
-  else
-    k_probe_adj<S, false><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p, pr.sites, pr.target,
-                                             pr.ax, pr.ay, pr.az, pr.invN, pr.np, (S*)mu);
+  PROBE_MODE_SWITCH(mode, (k_probe_adj<S, M><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p,
+                                                                 pr.sites, pr.target, pr.ax, pr.ay, pr.az, pr.invN,
+                                                                 pr.np, (S*)mu)));
   return cudaGetLastError();
 }
 
 struct AdjLayout {
   int64_t K = 1, nck = 1, nseg = 2;
-  size_t ck = 0, seg = 0, mu = 0, dtau = 0, dlink = 0, sites = 0, target = 0, jp = 0, gbegin = 0, out = 0, total = 0;
+  size_t ck = 0, seg = 0, mu = 0, dtau = 0, dlink = 0, sites = 0, target = 0, jp = 0, gbegin = 0, pmask = 0,
+         pbase = 0, out = 0, total = 0;
 };
 
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 AdjLayout adj_layout(const hlb_solver* h, int64_t N, int64_t np) {
   AdjLayout y;
+  // checkpoints are taken after odd AA steps, so the interval is even
   y.K = (int64_t)ceil(sqrt((double)N));
-  if (y.K < 1) y.K = 1;
+  if (y.K < 2) y.K = 2;
+  if (y.K & 1) ++y.K;
   y.nck = (N + y.K - 1) / y.K;
   y.nseg = std::max<int64_t>(y.K, 2);
   const size_t st = al256(h->state_bytes());
@@ -364,12 +453,14 @@ AdjLayout adj_layout(const hlb_solver* h, int64_t N, int64_t np) {
   y.ck = off; off += st * (size_t)y.nck;
   y.seg = off; off += st * (size_t)y.nseg;
   y.mu = off; off += st * 2;
-  y.dtau = off; off += al256(sizeof(double) * (grid_for(h->n) + (size_t)(h->n_iolet_sites + 127) / 128));
+  y.dtau = off; off += al256(sizeof(double) * (grid_for(h->n) + (size_t)(h->n_iolet_sites + 7) / 8));
   y.dlink = off; off += al256(sizeof(double) * (size_t)std::max<int64_t>(h->n_links, 1));
   y.sites = off; off += al256(sizeof(int64_t) * (size_t)std::max<int64_t>(np, 1));
   y.target = off; off += al256(sizeof(double) * (size_t)std::max<int64_t>(np, 1));
   y.jp = off; off += al256(sizeof(double) * (size_t)std::max<int64_t>(np, 1));
   y.gbegin = off; off += al256(sizeof(int64_t) * (size_t)(h->n_groups_total + 1));
+  y.pmask = off; off += al256(sizeof(uint32_t) * (size_t)((h->n + 31) / 32));
+  y.pbase = off; off += al256(sizeof(int32_t) * (size_t)((h->n + 31) / 32));
   y.out = off; off += al256(sizeof(double) * (size_t)(2 + h->n_groups_total));
   y.total = off;
   return y;
@@ -390,7 +481,7 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   double* jp = (double*)(ws + y.jp);
   int64_t* gbegin = (int64_t*)(ws + y.gbegin);
   double* out = (double*)(ws + y.out);
-  const int64_t nb = grid_for(h->n) + (h->n_iolet_sites + 127) / 128;  // bulk + iolet-site partials
+  const int64_t nb = grid_for(h->n) + (h->n_iolet_sites + 7) / 8;  // bulk + iolet-site partials
   const int64_t np = obj->n_probe;
   const int G = h->n_groups_total;
 
@@ -409,76 +500,92 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   TRY(cudaMemsetAsync(dtau_part, 0, sizeof(double) * nb, st));
   TRY(cudaMemsetAsync(dlink, 0, sizeof(double) * std::max<int64_t>(h->n_links, 1), st));
   TRY(cudaMemsetAsync(jp, 0, sizeof(double) * std::max<int64_t>(np, 1), st));
-  if (np > 0) {
-    TRY(cudaMemcpyAsync(d_sites, obj->sites, sizeof(int64_t) * np, cudaMemcpyHostToDevice, st));
-    TRY(cudaMemcpyAsync(d_target, obj->target, sizeof(double) * np, cudaMemcpyHostToDevice, st));
+  // probes ordered by site, and their bit mask with per-word prefix counts
+  std::vector<int64_t> order((size_t)np);
+  for (int64_t k = 0; k < np; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int64_t a_, int64_t b_) { return obj->sites[a_] < obj->sites[b_]; });
+  std::vector<int64_t> ssites((size_t)np);
+  std::vector<double> starget((size_t)np);
+  for (int64_t k = 0; k < np; ++k) {
+    ssites[k] = obj->sites[order[k]];
+    starget[k] = obj->target[order[k]];
   }
+  const int64_t nw = (h->n + 31) / 32;
+  std::vector<uint32_t> mask((size_t)nw, 0u);
+  std::vector<int32_t> base((size_t)nw, 0);
+  for (int64_t k = 0; k < np; ++k) mask[ssites[k] >> 5] |= 1u << (ssites[k] & 31);
+  for (int64_t wd = 1; wd < nw; ++wd) base[wd] = base[wd - 1] + __builtin_popcount(mask[wd - 1]);
+  uint32_t* d_mask = (uint32_t*)(ws + y.pmask);
+  int32_t* d_base = (int32_t*)(ws + y.pbase);
+  if (np > 0) {
+    TRY(cudaMemcpyAsync(d_sites, ssites.data(), sizeof(int64_t) * np, cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(d_target, starget.data(), sizeof(double) * np, cudaMemcpyHostToDevice, st));
+  }
+  TRY(cudaMemcpyAsync(d_mask, mask.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, st));
+  TRY(cudaMemcpyAsync(d_base, base.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
+  const ProbeMap pm{d_mask, d_base, d_target, obj->axis[0], obj->axis[1], obj->axis[2], 2.0 / (double)N};
   TRY(cudaMemcpyAsync(gbegin, h->group_link_begin.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, st));
   Probe pr{d_sites, d_target, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N, np};
 
-  // ---- forward: checkpoints every K steps, last segment kept whole ----
+  // ---- forward with the AA kernels on one working buffer; checkpoint c is
+  // the pre-collision state f(cK), taken after an odd step (natural layout) ----
   const int64_t K = y.K, nck = y.nck;
-  const int64_t last_begin = (nck - 1) * K;
-  const void* in = ck(0);
-  bool g = false;
-  int scratch = 0;
+  void* W = sg(0);
+  TRY(cudaMemcpyAsync(W, ck(0), h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+  bool swapped = false;
   for (int64_t s = 0; s < N; ++s) {
-    void* o;
-    if (s >= last_begin) {
-      o = sg(s - last_begin);
-    } else if ((s + 1) % K == 0) {
-      o = ck((s + 1) / K);
-    } else {
-      o = sg(scratch);
-      scratch ^= 1;
-    }
-    TRY(hlb_launch_step(h, in, o, g, t0 + s - 1, st));
-    TRY(launch_probe_obj<S>(h, o, true, t0 + s, pr, jp, st));
-    in = o;
-    g = true;
+    TRY(hlb_launch_aa(h, W, swapped, t0 + s, st));
+    swapped = !swapped;
+    TRY(launch_probe_obj<S>(h, W, swapped ? HLB_READ_GATHER_AA : HLB_READ_LOCAL, t0 + s, pr, jp, st));
+    if (!swapped && (s + 1) % K == 0 && (s + 1) / K < nck)
+      TRY(cudaMemcpyAsync(ck((s + 1) / K), W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
   }
+  // The final state f(t0 + N) goes straight into the solver's own buffer,
+  // which is free during the run (the start state was copied to checkpoint
+  // 0): AA keeps its layout, pull A-B receives the pre-collision form.
+  int fin_mode = swapped ? HLB_READ_GATHER_AA : HLB_READ_LOCAL;
+  if (h->scheme == HLB_AA || !swapped) {
+    TRY(cudaMemcpyAsync(h->f[0], W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+  } else {
+    TRY(hlb_launch_state(h, W, HLB_READ_GATHER_AA, t0 + N - 1, h->f[0], -1, st));
+    fin_mode = HLB_READ_LOCAL;
+  }
+  const void* fin_state = h->f[0];
 
-  // ---- reverse ----
+  // ---- reverse: recompute each segment's post-collision states with the
+  // pull kernels from its checkpoint, then sweep it backwards ----
   int a = 0;  // mu[a] holds mu(t+1)
   TRY(cudaMemsetAsync(mu[a], 0, h->state_bytes(), st));
-  TRY(launch_probe_adj<S>(h, in, true, t0 + N - 1, pr, mu[a], st));
+  TRY(launch_probe_adj<S>(h, fin_state, fin_mode, t0 + N - 1, pr, mu[a], st));
   for (int64_t c = nck - 1; c >= 0; --c) {
     const int64_t sb = c * K, se = std::min<int64_t>(N, (c + 1) * K);
-    if (c != nck - 1) {
-      const void* rin = ck(c);
-      bool rg = c > 0;
-      for (int64_t s = sb; s < se; ++s) {
-        TRY(hlb_launch_step(h, rin, sg(s - sb), rg, t0 + s - 1, st));
-        rin = sg(s - sb);
-        rg = true;
-      }
+    const void* rin = ck(c);
+    bool rg = false;
+    for (int64_t s = sb; s < se; ++s) {
+      TRY(hlb_launch_step(h, rin, sg(s - sb), rg, t0 + s - 1, st));
+      rin = sg(s - sb);
+      rg = true;
     }
     for (int64_t s = se - 1; s >= sb; --s) {
       const void* prev = s == sb ? ck(c) : sg(s - sb - 1);
-      const bool gprev = s != 0;
-      TRY(launch_adjoint<S>(h, prev, gprev, sg(s - sb), mu[a], mu[a ^ 1], t0 + s - 1, t0 + s, dtau_part, dlink,
+      const bool gprev = s != sb;  // a segment starts from its pre-collision checkpoint
+      // mu(s) = C^T G^T mu(s+1) + dJ/df(s) at the probes (s >= 1), in one pass
+      TRY(launch_adjoint<S>(h, prev, gprev, sg(s - sb), mu[a], mu[a ^ 1], t0 + s - 1, t0 + s, pm, dtau_part, dlink,
                             s >= 1, st));
-      if (s >= 1) TRY(launch_probe_adj<S>(h, prev, gprev, t0 + s - 1, pr, mu[a ^ 1], st));
       a ^= 1;
     }
   }
   k_adj_finish<<<2 + G, 256, 0, st>>>(jp, np, dtau_part, nb, dlink, gbegin, G, out);
   TRY(cudaGetLastError());
 
-  // leave the solver at t0 + N: A-B keeps the last post-collision state,
-  // AA receives the gathered pre-collision state f(t0 + N) in place
-  const void* last = sg(N - 1 - last_begin);
-  if (h->scheme == HLB_AA)
-    TRY(hlb_launch_state(h, last, HLB_READ_GATHER_AB, t0 + N - 1, h->f[0], -1, st));
-  else
-    TRY(cudaMemcpyAsync(h->f[0], last, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
   std::vector<double> host(2 + G);
   TRY(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
 #undef TRY
+  if (int rc = hlb_check_device_error(h)) return rc;
   h->cur = 0;
-  h->phase = h->scheme == HLB_AA ? HLB_READ_LOCAL : HLB_READ_GATHER_AB;
-  h->stepped = h->scheme != HLB_AA;
+  h->phase = fin_mode;
+  h->stepped = h->scheme == HLB_AA;
   h->t = t0 + N;
   if (J) *J = host[0];
   if (dtau_out) *dtau_out = host[1];

@@ -33,6 +33,14 @@ int hlb_cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 extern "C" const char* hlb_last_error(void) { return g_err.c_str(); }
+
+int hlb_check_device_error(hlb_solver* h) {
+  int flag = 0;
+  CUDA_TRY(cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (flag) return hlb_fail(HLB_ERR_CUDA, "a device wait for a staged index tile timed out; results are invalid");
+  return HLB_OK;
+}
 extern "C" int hlb_version(void) { return 10000; }
 
 // ---------------------------------------------------------------------------
@@ -87,6 +95,7 @@ StepParams hlb_solver::params(int64_t tb) const {
   StepParams p;
   memset(&p, 0, sizeof p);
   p.n = n;
+  p.sn = sn;
   p.omega = 1.0 / tau;
   p.n_iolets = n_iolets;
   p.ladd_rho_one = ladd_rho_one;
@@ -107,12 +116,16 @@ StepParams hlb_solver::params(int64_t tb) const {
 namespace {
 
 struct Layout {
-  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, total = 0;
+  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, err = 0,
+         total = 0;
   int64_t n_links = 0;
   int32_t n_groups = 0;
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+// Index rows are padded to a multiple of 4 entries (16 bytes) so that the
+// kernels can stage tiles of them with bulk copies.
+int64_t row_stride(int64_t n) { return (n + 3) & ~(int64_t)3; }
 
 int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* per_iolet_links,
              int64_t* n_iolet_sites) {
@@ -174,7 +187,7 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   size_t off = 0;
   y.f0 = off; off += state;
   y.f1 = off; off += resolve_scheme(o->scheme) == HLB_AA ? 0 : state;
-  y.src = off; off += align_up(sizeof(int32_t) * 18 * (size_t)n);
+  y.src = off; off += align_up(sizeof(int32_t) * 18 * (size_t)row_stride(n));
   y.links = off; off += align_up(sizeof(LinkRec) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.amp = off; off += align_up(sizeof(double) * (size_t)std::max(y.n_groups, 1));
   y.normal = off; off += L->wall_normal ? align_up(sizeof(float) * 3 * (size_t)n) : 0;
@@ -182,6 +195,7 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.red = off; off += align_up(sizeof(double) * (size_t)hlb_reduce_slots(n, L->n_iolets));
   y.lflux = off; off += align_up(sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.isites = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(n_iolet_sites, 1));
+  y.err = off; off += 256;
   y.total = off;
   return y;
 }
@@ -221,6 +235,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   if (!h) return hlb_fail(HLB_ERR_NOMEM, "host allocation failed");
   const int64_t n = L->n_sites;
   h->n = n;
+  h->sn = row_stride(n);
   h->n_iolets = L->n_iolets;
   h->iolets.assign(L->iolets, L->iolets + L->n_iolets);
   h->precision = o->precision;
@@ -256,6 +271,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->d_red = (double*)(base + y.red);
   h->red_slots = hlb_reduce_slots(n, h->n_iolets);
   h->d_lflux = (double*)(base + y.lflux);
+  h->d_err = (int*)(base + y.err);
   h->d_iolet_sites = (int32_t*)(base + y.isites);
   h->n_iolet_sites = nis;
 
@@ -285,7 +301,9 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
     }
   }
   std::vector<LinkRec> recs((size_t)std::max<int64_t>(y.n_links, 1));
-  std::vector<int32_t> src(L->src, L->src + (size_t)18 * n);
+  const int64_t sn = h->sn;
+  std::vector<int32_t> src((size_t)18 * sn, -1);  // padding entries are never gathered
+  for (int i = 0; i < 18; ++i) std::copy(L->src + (size_t)i * n, L->src + (size_t)(i + 1) * n, src.begin() + (size_t)i * sn);
   std::vector<int64_t> fillpos(count.begin(), count.end() - 1);
   for (int64_t x = 0; x < n; ++x)
     for (int j = 1; j < Q; ++j) {
@@ -318,7 +336,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
         // f_j(x) = f'_jbar(x) - 2 w rho (c_jbar . u_w) / cs2 = f'_jbar(x) + 6 w_j rho A W (c_j . n)
         R.coef = 6.0 * wgt<double>(j) * W * cn;
       }
-      src[(size_t)(j - 1) * n + x] = -(int32_t)(2 + r);
+      src[(size_t)(j - 1) * sn + x] = -(int32_t)(2 + r);
     }
 
   cudaStream_t st = h->stream;
@@ -334,7 +352,8 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
         break;
       }
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * 18 * (size_t)n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
   if (e == cudaSuccess && y.n_links > 0)
     e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(double) * ampf.size(), cudaMemcpyHostToDevice, st);
@@ -468,7 +487,7 @@ extern "C" int hlb_read_macros(hlb_solver* h, float* rho, float* u, float* wss, 
   if (u) CUDA_TRY(cudaMemcpyAsync(u, su, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
   if (wss) CUDA_TRY(cudaMemcpyAsync(wss, sw, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  return HLB_OK;
+  return hlb_check_device_error(h);
 }
 
 extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
@@ -479,6 +498,8 @@ extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
   std::vector<double> host(1 + h->n_iolets);
   CUDA_TRY(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  int rc = hlb_check_device_error(h);
+  if (rc) return rc;
   if (mass) *mass = host[0];
   if (flux)
     for (int k = 0; k < h->n_iolets; ++k) flux[k] = host[1 + k];
@@ -507,8 +528,8 @@ extern "C" int hlb_get_state(hlb_solver* h, void* f, int32_t where, int64_t* t) 
       CUDA_TRY(cudaMemcpyAsync((char*)f + row * i, h->d_stage, row, cudaMemcpyDeviceToHost, h->stream));
     }
   }
-  if (where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
   if (t) *t = h->t;
+  if (where == HLB_HOST) return hlb_check_device_error(h);
   return HLB_OK;
 }
 

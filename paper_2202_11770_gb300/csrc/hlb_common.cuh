@@ -101,6 +101,7 @@ struct IoletParam {
 
 struct StepParams {
   int64_t n;
+  int64_t sn;           // row stride of the index table: n rounded up to a multiple of 4
   double omega;         // 1 / tau
   int32_t n_iolets;
   int32_t ladd_rho_one;
@@ -179,12 +180,12 @@ __device__ __forceinline__ void collide(R* h, R omega) {
 // ---------------------------------------------------------------------------
 template <typename S>
 __device__ __forceinline__ bool gather_site(const S* __restrict__ fin, const int32_t* __restrict__ src,
-                                            int64_t n, int64_t x, typename Real<S>::type* h) {
+                                            int64_t n, int64_t sn, int64_t x, typename Real<S>::type* h) {
   h[0] = ldpop(fin + x);
   bool any_iolet = false;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    int32_t s = ldidx(src + (int64_t)(i - 1) * n + x);
+    int32_t s = ldidx(src + (int64_t)(i - 1) * sn + x);
     int64_t a = s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x;
     h[i] = ldpop(fin + a);
     any_iolet |= s <= -2;
@@ -194,13 +195,18 @@ __device__ __forceinline__ bool gather_site(const S* __restrict__ fin, const int
 
 // Boundary values of iolet links at site x (rare: only iolet sites).  On
 // entry h[i] of an iolet link already holds s'_ibar(x) (the gather selects
-// the own opposite slot for every non-fluid source).
+// the own opposite slot for every non-fluid source).  All index codes and
+// link records are loaded up front, independently of each other, so the
+// loads overlap instead of forming a chain per direction.
 template <typename S>
 __device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                             const LinkRec* __restrict__ links, const double* __restrict__ amp,
                                             const StepParams& p, int64_t x, typename Real<S>::type* h) {
   using R = typename Real<S>::type;
   const int64_t n = p.n;
+  int32_t code[Q];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) code[i] = src[(int64_t)(i - 1) * p.sn + x];
   // moments of the site's own post-collision state s'(t-1)
   R d = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
@@ -215,25 +221,234 @@ __device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int
   const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    int32_t s = src[(int64_t)(i - 1) * n + x];
-    if (s > -2) continue;
-    const LinkRec L = links[-s - 2];
-    const IoletParam io = p.io[L.iolet];
+    const bool io = code[i] <= -2;
+    const LinkRec L = links[io ? -code[i] - 2 : 0];       // record 0 exists whenever a site has an iolet link
+    const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+    if (!io) continue;
+    const IoletParam iop = p.io[L.iolet];
     if (L.kind == 0) {
       R rho = p.ladd_rho_one ? R(1) : rho_s;
-      h[i] += R(L.coef) * rho * R(amp[L.group]) * R(io.val);
+      h[i] += R(L.coef) * rho * R(a) * R(iop.val);
     } else {
       R gx = ux, gy = uy, gz = uz;
       if (!p.ghost_full_u) {
-        R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
-        gx = un * R(io.nx);
-        gy = un * R(io.ny);
-        gz = un * R(io.nz);
+        R un = gx * R(iop.nx) + gy * R(iop.ny) + gz * R(iop.nz);
+        gx = un * R(iop.nx);
+        gy = un * R(iop.ny);
+        gz = un * R(iop.nz);
       }
-      R drho = R(io.val);
+      R drho = R(iop.val);
       R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
       h[i] = heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative boundary sites: one warp per site, lane i = direction i
+// (lanes 19..31 idle).  Moments are summed by a shuffle loop in direction
+// order with exactly the operations of the per-thread code above, so a site
+// gets bit-identical values whichever path processes it.
+// ---------------------------------------------------------------------------
+constexpr unsigned FULL_MASK = 0xffffffffu;
+static __constant__ int8_t k_cx[32] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static __constant__ int8_t k_cy[32] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static __constant__ int8_t k_cz[32] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+__device__ __forceinline__ int lane_opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+template <typename R>
+__device__ __forceinline__ R lane_w(int i) {
+  return i == 0 ? R(1) / R(3) : (i <= 6 ? R(1) / R(18) : R(1) / R(36));
+}
+template <typename R>
+__device__ __forceinline__ R lane_cdotu(int i, R ux, R uy, R uz) {
+  R s = R(0);
+  if (k_cx[i]) s += k_cx[i] > 0 ? ux : -ux;
+  if (k_cy[i]) s += k_cy[i] > 0 ? uy : -uy;
+  if (k_cz[i]) s += k_cz[i] > 0 ? uz : -uz;
+  return s;
+}
+template <typename R>
+__device__ __forceinline__ R lane_heq(int i, R drho, R rho, R ux, R uy, R uz, R usq15) {
+  R cu = lane_cdotu<R>(i, ux, uy, uz);
+  return lane_w<R>(i) * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
+}
+// sum over lanes 0..18 of v (direction order), every lane gets the result
+template <typename R>
+__device__ __forceinline__ R lane_sum(R v) {
+  R acc = R(0);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) acc += __shfl_sync(FULL_MASK, v, k);
+  return acc;
+}
+// (sum v, sum v c) over lanes 0..18 in direction order; sgn = -1 sums -v c
+template <typename R>
+__device__ __forceinline__ void lane_moment_sums(R v, R sgn, R* d, R* jx, R* jy, R* jz) {
+  R a = R(0), x = R(0), y = R(0), z = R(0);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const R vk = __shfl_sync(FULL_MASK, v, k);
+    a += vk;
+    if (cx(k)) x += (cx(k) > 0) == (sgn > R(0)) ? vk : -vk;
+    if (cy(k)) y += (cy(k) > 0) == (sgn > R(0)) ? vk : -vk;
+    if (cz(k)) z += (cz(k) > 0) == (sgn > R(0)) ? vk : -vk;
+  }
+  *d = a; *jx = x; *jy = y; *jz = z;
+}
+// moments() of a distributed vector (u = j * (1/rho), as moments() does)
+template <typename R>
+__device__ __forceinline__ Macro<R> lane_moments(R v) {
+  Macro<R> m;
+  R jx, jy, jz;
+  lane_moment_sums<R>(v, R(1), &m.drho, &jx, &jy, &jz);
+  m.rho = R(1) + m.drho;
+  const R inv = R(1) / m.rho;
+  m.ux = jx * inv;
+  m.uy = jy * inv;
+  m.uz = jz * inv;
+  return m;
+}
+// Boundary value of the lane's iolet link (as iolet_fixup computes it):
+// `out` = s'_ibar(x); rho_s, u_s the moments of the stored post-collision state.
+template <typename R>
+__device__ __forceinline__ R lane_iolet_value(int i, const LinkRec& L, R out, R rho_s, R ux, R uy, R uz, double a,
+                                              const StepParams& p) {
+  const IoletParam iop = p.io[L.iolet];
+  if (L.kind == 0) {
+    R rho = p.ladd_rho_one ? R(1) : rho_s;
+    return out + R(L.coef) * rho * R(a) * R(iop.val);
+  }
+  R gx = ux, gy = uy, gz = uz;
+  if (!p.ghost_full_u) {
+    R un = gx * R(iop.nx) + gy * R(iop.ny) + gz * R(iop.nz);
+    gx = un * R(iop.nx);
+    gy = un * R(iop.ny);
+    gz = un * R(iop.nz);
+  }
+  R drho = R(iop.val);
+  R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
+  return lane_heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
+}
+
+// ---------------------------------------------------------------------------
+// Reading f(t) from a population buffer (read modes of hlb_internal.h:
+// 0 = in place, 1 = pull A-B gather with boundaries, 2 = AA gather).
+// ---------------------------------------------------------------------------
+// Address of slot i of site x in an odd step (and in an AA read-back): the
+// population arriving along c_i was written by the source x - c_i into its
+// opposite slot, or, for a non-fluid source, by x itself into slot i.
+__device__ __forceinline__ int64_t aa_addr(int i, int32_t s, int64_t n, int64_t x) {
+  return s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x;
+}
+
+template <typename S, int MODE>
+__device__ __forceinline__ void load_state(const S* __restrict__ fin, const int32_t* __restrict__ src,
+                                           const LinkRec* __restrict__ links, const double* __restrict__ amp,
+                                           const StepParams& p, int64_t x, typename Real<S>::type* h) {
+  if (MODE == 1) {
+    if (gather_site<S>(fin, src, p.n, p.sn, x, h)) iolet_fixup<S>(fin, src, links, amp, p, x, h);
+  } else if (MODE == 2) {
+    h[0] = ldpop(fin + x);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) h[i] = ldpop(fin + aa_addr(i, src[(int64_t)(i - 1) * p.sn + x], p.n, x));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * p.n + x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Index tiles staged in shared memory by the Tensor Memory Accelerator.
+//
+// Persistent kernels walk tiles of TILE consecutive sites; one thread per CTA
+// copies the next tile's 18 index rows (18 x TILE int32, contiguous in each
+// row) into the other half of a double buffer with cp.async.bulk, completing
+// on an mbarrier, while the CTA works on the current tile.  Index rows have
+// a stride that is a multiple of 4 sites and tiles start at multiples of
+// TILE, so every copy starts on a 16-byte boundary and moves a multiple of
+// 16 bytes.  Waits are bounded: a wait that runs out records an error in
+// *err and the tile is skipped (no index from an unfinished copy is used).
+// ---------------------------------------------------------------------------
+constexpr int TILE = 256;
+constexpr int WAIT_LIMIT = 1 << 22;
+
+// 128-byte aligned: bulk-copy destinations must start on 16-byte boundaries
+// (each row is TILE * 4 = 1 KiB, so every row start stays aligned).
+struct __align__(128) IdxTiles {
+  int32_t idx[2][Q - 1][TILE];
+  unsigned long long bar[2];
+};
+static_assert(sizeof(int32_t) * TILE % 16 == 0, "index rows must keep 16-byte alignment");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tile_init(IdxTiles& t) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&t.bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&t.bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// One thread: stage the index rows of `tile` into buffer b.
+__device__ __forceinline__ void tile_issue(IdxTiles& t, int b, const int32_t* __restrict__ src, int64_t n,
+                                           int64_t sn, int64_t tile) {
+  const int64_t start = tile * TILE;
+  const int64_t left = n - start;
+  const uint32_t cnt = (uint32_t)(left < TILE ? ((left + 3) & ~(int64_t)3) : TILE);
+  const uint32_t bytes = cnt * 4u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
+               ::"r"(smem_addr(&t.bar[b])), "r"(bytes * (Q - 1)) : "memory");
+#pragma unroll 1
+  for (int i = 0; i < Q - 1; ++i)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(&t.idx[b][i][0])), "l"(src + (int64_t)i * sn + start), "r"(bytes),
+                 "r"(smem_addr(&t.bar[b]))
+                 : "memory");
+}
+
+// All threads: wait (bounded) for buffer b's copy of the given phase parity.
+__device__ __forceinline__ bool tile_wait(IdxTiles& t, int b, uint32_t parity, int* err) {
+  for (int it = 0; it < WAIT_LIMIT; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(smem_addr(&t.bar[b])), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  atomicExch(err, 1);
+  return false;
+}
+
+// Persistent tile loop shared by the gather kernels: for every tile owned by
+// this CTA, stage its index rows (prefetching the next tile's), then call
+// body(x, codes_row0, ok).  `ok` is false only when the index copy did not
+// complete in time (the error word is set and the tile is skipped).
+template <typename Body>
+__device__ __forceinline__ void tile_loop(IdxTiles& t, const int32_t* __restrict__ src, int64_t n, int64_t sn,
+                                          int* err, Body body) {
+  const int64_t ntiles = (n + TILE - 1) / TILE;
+  tile_init(t);
+  int64_t tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) tile_issue(t, 0, src, n, sn, tile);
+  int b = 0;
+  uint32_t par0 = 0u, par1 = 0u;  // phase parity expected next on each buffer's barrier
+  bool missed = false;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int64_t next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) tile_issue(t, b ^ 1, src, n, sn, next);
+    const bool ok = tile_wait(t, b, b ? par1 : par0, err);
+    missed |= !ok;
+    if (b) par1 ^= 1u; else par0 ^= 1u;
+    body(tile * TILE + threadIdx.x, &t.idx[b][0][threadIdx.x], ok);
+    __syncthreads();  // every thread is done with buffer b before it is refilled
+    b ^= 1;
+  }
+  // a copy that timed out may still be in flight: wait for it (bounded) before leaving
+  if (missed && threadIdx.x == 0) {
+    tile_wait(t, 0, par0 ^ 1u, err);
+    tile_wait(t, 1, par1 ^ 1u, err);
   }
 }
 

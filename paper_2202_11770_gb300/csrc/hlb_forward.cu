@@ -34,40 +34,93 @@ constexpr int BLOCK = 256;
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
 // ---------------------------------------------------------------------------
-// Pull A-B step.  GATHER = false: the buffer holds the pre-collision state
-// f(t) (after initialisation or set_state); GATHER = true: it holds s'(t-1).
+// Pull A-B step from f(t) held in place (the first step after initialisation
+// or set_state): no gather.
 // ---------------------------------------------------------------------------
-template <typename S, bool GATHER>
-__global__ void __launch_bounds__(BLOCK) k_step(const S* __restrict__ fin, S* __restrict__ fout,
-                                                const int32_t* __restrict__ src,
-                                                const LinkRec* __restrict__ links,
-                                                const double* __restrict__ amp, const StepParams p) {
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_step_local(const S* __restrict__ fin, S* __restrict__ fout,
+                                                      const StepParams p) {
   using R = typename Real<S>::type;
   const int64_t n = p.n;
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (x >= n) return;
   R h[Q];
-  if (GATHER) {
-    if (gather_site<S>(fin, src, n, x, h)) iolet_fixup<S>(fin, src, links, amp, p, x, h);
-  } else {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * n + x);
-  }
+  for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * n + x);
   collide<R>(h, R(p.omega));
 #pragma unroll
   for (int i = 0; i < Q; ++i) stpop<S>(fout + (int64_t)i * n + x, h[i]);
 }
 
+// Pull A-B step from s'(t-1): gather f(t) through the staged index tile,
+// collide, store.  Sites with iolet links are written by k_step_iolet.
+template <typename S>
+__global__ void __launch_bounds__(TILE, 5) k_step(const S* __restrict__ fin, S* __restrict__ fout,
+                                               const int32_t* __restrict__ src, const StepParams p, int* err) {
+  using R = typename Real<S>::type;
+  __shared__ IdxTiles t;
+  const int64_t n = p.n;
+  tile_loop(t, src, n, p.sn, err, [&](int64_t x, const int32_t* codes, bool ok) {
+    if (!ok || x >= n) return;
+    R h[Q];
+    h[0] = ldpop(fin + x);
+    bool iolet = false;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int32_t s = codes[(i - 1) * TILE];
+      h[i] = ldpop(fin + (s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x));
+      iolet |= s <= -2;
+    }
+    collide<R>(h, R(p.omega));
+    if (iolet) return;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) stpop<S>(fout + (int64_t)i * n + x, h[i]);
+  });
+}
+
+// The same step for the sites with iolet links: one warp per site, lane i
+// handles direction i (gather, boundary value, collision), with the moment
+// sums in direction order so that every value equals the per-thread
+// read-back path (iolet_fixup) bit for bit.
+template <typename S>
+__global__ void __launch_bounds__(256) k_step_iolet(const S* __restrict__ fin, S* __restrict__ fout,
+                                                    const int32_t* __restrict__ src,
+                                                    const LinkRec* __restrict__ links,
+                                                    const double* __restrict__ amp,
+                                                    const int32_t* __restrict__ sites, int64_t nsites,
+                                                    const StepParams p) {
+  using R = typename Real<S>::type;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nsites) return;  // uniform across the warp
+  const int i = threadIdx.x & 31;
+  const bool dir = i < Q;
+  const int64_t n = p.n, x = sites[w];
+  const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
+  R h = R(0), own = R(0);
+  if (dir) {
+    h = ldpop(fin + (i == 0 ? x : (code >= 0 ? (int64_t)i * n + code : (int64_t)lane_opp(i) * n + x)));
+    own = ldpop(fin + (int64_t)i * n + x);
+  }
+  R d, jx, jy, jz;
+  lane_moment_sums<R>(own, R(1), &d, &jx, &jy, &jz);
+  const R rho_s = R(1) + d;
+  const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
+  if (code <= -2) {
+    const LinkRec L = links[-code - 2];
+    const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+    h = lane_iolet_value<R>(i, L, h, rho_s, ux, uy, uz, a, p);
+  }
+  const Macro<R> m = lane_moments<R>(h);
+  const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+  if (dir) {
+    h += R(p.omega) * (lane_heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15) - h);
+    stpop<S>(fout + (int64_t)i * n + x, h);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // AA pattern.
 // ---------------------------------------------------------------------------
-// Address of slot i of site x in an odd step (and in an AA read-back): the
-// population arriving along c_i was written by the source x - c_i into its
-// opposite slot, or, for a non-fluid source, by x itself into slot i.
-__device__ __forceinline__ int64_t aa_addr(int i, int32_t s, int64_t n, int64_t x) {
-  return s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x;
-}
-
 // Even step: f(t) in place -> collide -> s'(t) stored swapped (slot ibar).
 template <typename S>
 __global__ void __launch_bounds__(BLOCK) k_aa_even(S* A, const StepParams p) {
@@ -81,6 +134,42 @@ __global__ void __launch_bounds__(BLOCK) k_aa_even(S* A, const StepParams p) {
   collide<R>(h, R(p.omega));
 #pragma unroll
   for (int i = 0; i < Q; ++i) stpop<S>(A + (int64_t)opp(i) * n + x, h[i]);
+}
+
+// Even step for 16-bit storage, two neighbouring sites per thread with 4-byte
+// accesses (rows are 4-byte aligned when n is even).
+template <typename S> struct Pair;
+template <> struct Pair<__nv_bfloat16> {
+  using T = __nv_bfloat162;
+  static __device__ __forceinline__ float2 to(T v) { return __bfloat1622float2(v); }
+  static __device__ __forceinline__ T from(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <> struct Pair<__half> {
+  using T = __half2;
+  static __device__ __forceinline__ float2 to(T v) { return __half22float2(v); }
+  static __device__ __forceinline__ T from(float a, float b) { return __floats2half2_rn(a, b); }
+};
+
+template <typename S>
+__global__ void __launch_bounds__(BLOCK) k_aa_even2(S* A, const StepParams p) {
+  using P = Pair<S>;
+  using T = typename P::T;
+  const int64_t n = p.n;
+  const int64_t x = 2 * ((int64_t)blockIdx.x * BLOCK + threadIdx.x);
+  if (x >= n) return;
+  T* A2 = reinterpret_cast<T*>(A);
+  const int64_t n2 = n / 2, x2 = x / 2;
+  float a[Q], b[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float2 v = P::to(A2[(int64_t)i * n2 + x2]);
+    a[i] = v.x;
+    b[i] = v.y;
+  }
+  collide<float>(a, float(p.omega));
+  collide<float>(b, float(p.omega));
+#pragma unroll
+  for (int i = 0; i < Q; ++i) __stcs(A2 + (int64_t)opp(i) * n2 + x2, P::from(a[i], b[i]));
 }
 
 // Boundary value of iolet link (pull direction i, record L) at a site whose
@@ -108,43 +197,36 @@ __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, 
 
 // After an AA step at time t: overwrite the slots that the iolet links of
 // each iolet site read in the next step with their boundary values, and
-// record the mass each link lets in.  One thread per iolet site.  The site's
-// stored post-collision populations s'_ibar(x) sit in slot i of x after an
-// even step, and in the slot it read direction i from after an odd step; an
-// iolet link's slot is slot i of x in both cases.  Boundary values use the
-// moments of these stored values, as the A-B gather does.
+// record the mass each link lets in.  One warp per iolet site, lane i =
+// direction i.  The site's stored post-collision populations s'_ibar(x) sit
+// in slot i of x after an even step, and in the slot it read direction i from
+// after an odd step; an iolet link's slot is slot i of x in both cases.
+// Boundary values use the moments of these stored values, as the A-B gather
+// does.
 template <typename S, bool ODD>
-__global__ void k_aa_fix(S* A, const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
-                         const double* __restrict__ amp, const int32_t* __restrict__ sites, int64_t nsites,
-                         const StepParams p, double* __restrict__ lflux) {
+__global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict__ src,
+                                                const LinkRec* __restrict__ links, const double* __restrict__ amp,
+                                                const int32_t* __restrict__ sites, int64_t nsites,
+                                                const StepParams p, double* __restrict__ lflux) {
   using R = typename Real<S>::type;
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nsites) return;
-  const int64_t n = p.n;
-  const int64_t x = sites[q];
-  R v[Q];
-  v[0] = to_real(A[x]);
-#pragma unroll
-  for (int i = 1; i < Q; ++i)
-    v[i] = to_real(A[ODD ? aa_addr(i, src[(int64_t)(i - 1) * n + x], n, x) : (int64_t)i * n + x]);
-  // v[k] = s'_kbar(x): rho = 1 + sum v, j = -sum v_k c_k
-  R d = R(0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    d += v[k];
-    if (cx(k)) jx += cx(k) > 0 ? -v[k] : v[k];
-    if (cy(k)) jy += cy(k) > 0 ? -v[k] : v[k];
-    if (cz(k)) jz += cz(k) > 0 ? -v[k] : v[k];
-  }
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nsites) return;  // uniform across the warp
+  const int i = threadIdx.x & 31;
+  const bool dir = i < Q;
+  const int64_t n = p.n, x = sites[w];
+  const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
+  R v = R(0);
+  if (dir) v = to_real(A[i == 0 ? x : (ODD ? aa_addr(i, code, n, x) : (int64_t)i * n + x)]);
+  // v = s'_ibar(x): rho = 1 + sum v, j = -sum v_i c_i
+  R d, jx, jy, jz;
+  lane_moment_sums<R>(v, R(-1), &d, &jx, &jy, &jz);
   const R rho = R(1) + d;
   const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int32_t s = src[(int64_t)(i - 1) * n + x];
-    if (s > -2) continue;
-    const LinkRec L = links[-s - 2];
-    const R val = iolet_value<R>(i, L, v[i], rho, ux, uy, uz, amp, p);
-    lflux[-s - 2] = (double)val - (double)v[i];
+  if (code <= -2) {
+    const LinkRec L = links[-code - 2];
+    const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+    const R val = lane_iolet_value<R>(i, L, v, rho, ux, uy, uz, a, p);
+    lflux[-code - 2] = (double)val - (double)v;
     A[(int64_t)i * n + x] = from_real<S>(val);
   }
 }
@@ -153,44 +235,31 @@ __global__ void k_aa_fix(S* A, const int32_t* __restrict__ src, const LinkRec* _
 // post-collision population into the slot it came from, where the site
 // downstream (or, across a wall or iolet, the site itself) reads it in the
 // next (even) step.  Iolet links get their boundary values from k_aa_fix.
-template <typename S>
-__global__ void __launch_bounds__(BLOCK) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
+// The index table is read again for the store addresses (the same 72 bytes,
+// served from cache) rather than held in registers across the collision;
+// 4 resident blocks per SM measured fastest (a small spill is cheaper than
+// the lost occupancy).
+// SAME_STRIDE: the index rows are not padded (n is a multiple of 4), so one
+// row stride serves both arrays and fewer 64-bit row offsets stay live.
+template <typename S, bool SAME_STRIDE>
+__global__ void __launch_bounds__(BLOCK, 4) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
   using R = typename Real<S>::type;
-  const int64_t n = p.n;
+  const int64_t n = p.n, sn = SAME_STRIDE ? p.n : p.sn;
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   if (x >= n) return;
   R h[Q];
   h[0] = to_real(A[x]);
 #pragma unroll
-  for (int i = 1; i < Q; ++i) h[i] = to_real(A[aa_addr(i, __ldg(src + (int64_t)(i - 1) * n + x), n, x)]);
+  for (int i = 1; i < Q; ++i) h[i] = to_real(A[aa_addr(i, __ldg(src + (int64_t)(i - 1) * sn + x), n, x)]);
   collide<R>(h, R(p.omega));
   stpop<S>(A + x, h[0]);
-  // The index table is read again for the store addresses rather than kept
-  // in registers across the collision: the same 72 bytes this thread has just
-  // read, served from L1/L2.
 #pragma unroll
-  for (int i = 1; i < Q; ++i) stpop<S>(A + aa_addr(i, __ldg(src + (int64_t)(i - 1) * n + x), n, x), h[opp(i)]);
+  for (int i = 1; i < Q; ++i) stpop<S>(A + aa_addr(i, __ldg(src + (int64_t)(i - 1) * sn + x), n, x), h[opp(i)]);
 }
 
 // ---------------------------------------------------------------------------
 // Read-back kernels.
 // ---------------------------------------------------------------------------
-template <typename S, int MODE>
-__device__ __forceinline__ void load_state(const S* __restrict__ fin, const int32_t* __restrict__ src,
-                                           const LinkRec* __restrict__ links, const double* __restrict__ amp,
-                                           const StepParams& p, int64_t x, typename Real<S>::type* h) {
-  if (MODE == HLB_READ_GATHER_AB) {
-    if (gather_site<S>(fin, src, p.n, x, h)) iolet_fixup<S>(fin, src, links, amp, p, x, h);
-  } else if (MODE == HLB_READ_GATHER_AA) {
-    h[0] = ldpop(fin + x);
-#pragma unroll
-    for (int i = 1; i < Q; ++i) h[i] = ldpop(fin + aa_addr(i, src[(int64_t)(i - 1) * p.n + x], p.n, x));
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * p.n + x);
-  }
-}
-
 // Density, velocity and wall shear stress of f(t).
 template <typename S, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, const int32_t* __restrict__ src,
@@ -218,7 +287,7 @@ __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, con
   R nx = 0, ny = 0, nz = 0;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    if (src[(int64_t)(i - 1) * n + x] == -1) {
+    if (src[(int64_t)(i - 1) * p.sn + x] == -1) {
       wall = true;
       nx += R(cx(i));
       ny += R(cy(i));
@@ -407,6 +476,24 @@ __global__ void k_zero(double* p, int64_t m) {
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
+// Grid of a persistent tile kernel: resident CTAs per SM x SMs, capped by
+// the number of tiles.  Cached per kernel and device.
+template <typename K>
+unsigned persistent_grid(const hlb_solver* h, K kernel) {
+  static int cache[64] = {0};
+  const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
+  if (!cache[dev]) {
+    int sms = 0, occ = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // prefer the largest shared-memory carveout: these kernels stage index tiles
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TILE, 0);
+    cache[dev] = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
+  }
+  const int64_t ntiles = (h->n + TILE - 1) / TILE;
+  return (unsigned)(ntiles < cache[dev] ? ntiles : cache[dev]);
+}
+
 template <template <typename> class F, typename... A>
 cudaError_t dispatch(int precision, A... a) {
   switch (precision) {
@@ -423,29 +510,55 @@ struct StepOp {
   static cudaError_t run(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
                          cudaStream_t s) {
     StepParams p = h->params(tb);
-    if (gather)
-      k_step<S, true><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, p);
-    else
-      k_step<S, false><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, p);
+    if (gather) {
+      k_step<S><<<persistent_grid(h, k_step<S>), TILE, 0, s>>>((const S*)fin, (S*)fout, h->d_src, p, h->d_err);
+      if (h->n_iolet_sites > 0)
+        k_step_iolet<S><<<(unsigned)((h->n_iolet_sites + 7) / 8), 256, 0, s>>>(
+            (const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites, h->n_iolet_sites, p);
+    } else {
+      k_step_local<S><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, p);
+    }
     return cudaGetLastError();
   }
 };
+
+template <typename S>
+void aa_even(const hlb_solver* h, S* A, const StepParams& p, cudaStream_t s) {
+  k_aa_even<S><<<grid_for(h->n), BLOCK, 0, s>>>(A, p);
+}
+template <>
+void aa_even<__nv_bfloat16>(const hlb_solver* h, __nv_bfloat16* A, const StepParams& p, cudaStream_t s) {
+  if (h->n % 2 == 0)
+    k_aa_even2<__nv_bfloat16><<<grid_for(h->n / 2), BLOCK, 0, s>>>(A, p);
+  else
+    k_aa_even<__nv_bfloat16><<<grid_for(h->n), BLOCK, 0, s>>>(A, p);
+}
+template <>
+void aa_even<__half>(const hlb_solver* h, __half* A, const StepParams& p, cudaStream_t s) {
+  if (h->n % 2 == 0)
+    k_aa_even2<__half><<<grid_for(h->n / 2), BLOCK, 0, s>>>(A, p);
+  else
+    k_aa_even<__half><<<grid_for(h->n), BLOCK, 0, s>>>(A, p);
+}
 
 template <typename S>
 struct AAOp {
   static cudaError_t run(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
     StepParams p = h->params(t);
     if (odd)
-      k_aa_odd<S><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
+      if (h->sn == h->n)
+        k_aa_odd<S, true><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
+      else
+        k_aa_odd<S, false><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
     else
-      k_aa_even<S><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, p);
+      aa_even<S>(h, (S*)A, p, s);
     if (h->n_iolet_sites > 0) {
-      const unsigned g = (unsigned)((h->n_iolet_sites + 127) / 128);
+      const unsigned g = (unsigned)((h->n_iolet_sites + 7) / 8);  // 8 warps (sites) per block
       if (odd)
-        k_aa_fix<S, true><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+        k_aa_fix<S, true><<<g, 256, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
                                             h->n_iolet_sites, p, h->d_lflux);
       else
-        k_aa_fix<S, false><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+        k_aa_fix<S, false><<<g, 256, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
                                              h->n_iolet_sites, p, h->d_lflux);
     }
     return cudaGetLastError();
