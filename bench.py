@@ -385,18 +385,19 @@ def run_ours(args):
     scheme = args.scheme
     clocks = ClockSampler(local)
     clocks.start()
-    ms, durs, t_first = time_form(lat, "fp32", scheme, args.steps, args.warmup, torch, dist)
+    prec0 = args.precision if args.quick else "fp32"
+    ms, durs, t_first = time_form(lat, prec0, scheme, args.steps, args.warmup, torch, dist)
     clk = clocks.stop()
     ms, total_updates = aggregate_ranks(ms, n * args.steps, dist, "cuda")
     value = total_updates / (ms * 1e-3) / 1e6
-    head = form_stats(lat, "fp32", scheme, ms, durs, t_first, args.steps, peak)
+    head = form_stats(lat, prec0, scheme, ms, durs, t_first, args.steps, peak)
     kname = "k_step" if scheme == "ab" else "k_aa_odd"
     kst = head["kernels"][kname]
     traffic = None
     if TRAFFIC["sha"] == kernel_sha() and kname in TRAFFIC["bytes_per_site"]:
         traffic = TRAFFIC["bytes_per_site"][kname] * n
 
-    forms = {f"fp32_{scheme}": head}
+    forms = {f"{prec0}_{scheme}": head}
     if not args.quick:
         for prec in ("fp32", "bf16", "fp16"):
             for sch in ("ab", "aa"):
@@ -425,7 +426,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 storage, f32 math", "fp16": "f16 storage, f32 math", "fp64": "f64"}[prec0], "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_sites": n, "tau": 0.55,
                        "scheme": {"ab": "pull A-B", "aa": "AA pattern"}[scheme],
                        "parallelism": f"replicas x{world}", "l2": "working set 4.5 GB/step >> 129 MB L2, no flush",
@@ -438,7 +439,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
-            "gpu_launches": args.steps if scheme == "ab" else args.steps + head["kernels"]["k_aa_even+fix"]["launches"],
+            # per step: the bulk kernel and the iolet-site kernel (A-B) or fix-up pass (AA)
+            "gpu_launches": args.steps * (2 if bool((lat.src <= -2).any()) else 1),
             "forms": forms,
             "adjoint": adjoint,
         }
@@ -464,7 +466,9 @@ def main():
                     help="u and WSS error of FP32/BF16/FP16 storage vs FP64 at 1k, 5k, 10k steps")
     ap.add_argument("--ref-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="FP32 only, no e2e (profiling runs)")
+    ap.add_argument("--quick", action="store_true", help="one form only, no e2e (profiling runs)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"],
+                    help="storage precision of the one form timed by --quick")
     ap.add_argument("--scheme", default="aa", choices=["ab", "aa"],
                     help="streaming scheme of the headline FP32 form (the solver's AUTO choice is aa)")
     args = ap.parse_args()

@@ -243,6 +243,85 @@ def test_16bit_storage_error_reported(pipe, prec, bound, scheme):
     assert err < bound
 
 
+def _stored_to_f64(a, prec):
+    if prec == "bf16":
+        return hemegb.bf16_to_float(a).astype(np.float64)
+    return a.astype(np.float64)
+
+
+def _half_ulp(v, prec):
+    """Half a unit in the last place of the 16-bit format at magnitude |v|."""
+    mant, emin = (7, -126) if prec == "bf16" else (10, -14)
+    e = np.floor(np.log2(np.maximum(np.abs(v), 2.0 ** emin)))
+    return 0.5 * 2.0 ** (e - mant)
+
+
+def _one_step_within_rounding(lat, tau, bc, prec, scheme, w, warm=5):
+    """Step the 16-bit solver `warm` steps, then compare one more step with
+    the oracle's FP64 step from the same (exactly representable) state.
+
+    Tight entries: a stored value is the FP64 result rounded to the 16-bit
+    format, up to the FP32 collision arithmetic (delta) before the rounding.
+    Loose entries (iolet links, and values copied from an iolet site): the
+    solver computes boundary values in FP32 from its rounded stored state
+    and collides with them unrounded, while the state handed to the oracle
+    carries them rounded.  Each such input is off by at most half an ulp of
+    the site's largest value; through the moments (d u / d s'_j = (c_j - u)/rho,
+    sum |c_j| < 24) and the equilibrium's sensitivity (w_i rho |d feq/d u|
+    < 0.3, and < 7 w_i per unit of input in the collision) that is below 16
+    such half-ulps on the result."""
+    s = hemegb.Solver(lat, tau=tau, precision=prec, scheme=scheme)
+    bc(s)
+    s.init_equilibrium()
+    s.step(warm)
+    h5, t5 = s.state()
+    s.step(1)
+    h6, _ = s.state()
+    o = oracle.Oracle(lat, tau=tau)
+    bc(o)
+    o.set_state((_stored_to_f64(h5, prec) + w[:, None]).T, t5)
+    o.step(1)
+    ref = o.state().T - w[:, None]
+    got = _stored_to_f64(h6, prec)
+    delta = 5e-8
+    bound = _half_ulp(np.abs(ref) + delta, prec) + delta
+
+    n = lat.n
+    src = lat.src
+    iolet_site = (src <= -2).any(axis=0)
+    y = np.where(src >= 0, src, np.arange(n)[None, :])  # site whose s'(t) f_i(x) copies
+    loose = np.empty((19, n), bool)
+    loose[0] = iolet_site
+    loose[1:] = iolet_site[y] | (src <= -2)
+    site_max = np.abs(ref).max(axis=0)
+    mag = np.maximum(site_max[None, :], np.concatenate([site_max[None, :], site_max[y]]))
+    bound = np.where(loose, bound + 16 * _half_ulp(mag, prec), bound)
+    assert loose.mean() < 0.05
+    excess = np.abs(got - ref) - bound
+    k = np.unravel_index(excess.argmax(), excess.shape)
+    assert excess.max() <= 0.0, f"worst excess {excess.max():.3e} at {k} (loose={loose[k]})"
+    tight = ~loose
+    print(f"{prec}/{scheme}: max |err|/half-ulp on tight entries "
+          f"{(np.abs(got - ref)[tight] / _half_ulp(np.abs(ref[tight]) + delta, prec)).max():.3f}, "
+          f"loose entries {loose.mean():.2%}")
+    return o
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_16bit_one_step_within_storage_rounding(d3q19, prec, scheme):
+    """Ragged several-tile tree (pulsatile inlet, 7 pressure outlets)."""
+    _, w = d3q19
+    lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0)
+    assert lat.n % 256
+
+    def bc(x):
+        x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 200.0})
+        for k in range(1, len(lat.iolets)):
+            x.set_pressure(k, 1.0)
+    _one_step_within_rounding(lat, 0.55, bc, prec, scheme, w, warm=6 if scheme == "aa" else 5)
+
+
 def test_invalid_arguments(pipe):
     s = hemegb.Solver(pipe, tau=0.8)
     with pytest.raises(hemegb.HlbError):
@@ -294,3 +373,16 @@ def test_full_size_tree_one_step_vs_oracle(d3q19, scheme, tree20m):
     diff = np.abs(f6.T.astype(np.float64) + w[None, :] - f6o)
     assert diff.max() < 2e-8
     assert abs(o.mass() - m6) < 1e-9 * m6
+
+
+def test_full_size_tree_one_step_bf16_aa(d3q19, tree20m):
+    """Full-size 20M-site tree with BF16 storage in the benchmark's default
+    scheme: one step within storage rounding of the oracle at every site."""
+    _, w = d3q19
+    lat = tree20m
+
+    def bc(x):
+        x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 2000.0})
+        for k in range(1, len(lat.iolets)):
+            x.set_pressure(k, 1.0)
+    _one_step_within_rounding(lat, 0.55, bc, "bf16", "aa", w)
