@@ -73,51 +73,49 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
-// Bulk reverse step over all sites without iolet links: a persistent tile
-// loop whose staged index tile serves both gathers.  f(t) is gathered from
-// s'(t-1) first; its moments are kept and its non-equilibrium parts
-// h_i - heq_i are parked in shared memory, so that the 19 gathered values of
-// mu(t+1) can reuse the registers (keeping both 19-vectors live would halve
-// the resident warps).  Then lam = G_t^T mu(t+1) and
-// mu_j(t) = (1 - omega) lam_j + omega (S0 + (c_j - u).B).
-template <typename S, bool GPREV>
-__global__ void __launch_bounds__(TILE, sizeof(typename Real<S>::type) == 8 ? 1 : 3) k_adjoint(const S* __restrict__ prev, const S* __restrict__ mu_next,
-                                                  S* __restrict__ mu_out, const int32_t* __restrict__ src,
-                                                  const AdjParams ap, const ProbeMap pm, double* __restrict__ dtau_part,
-                                                  int store, int* err) {
+// Bulk reverse step over all sites without iolet links, one site per
+// thread.  f(t) is gathered from s'(t-1) first; its moments are kept and its
+// non-equilibrium parts h_i - heq_i are parked in shared memory, so that the
+// 19 gathered values of mu(t+1) can reuse the registers.  Then
+// lam = G_t^T mu(t+1) and mu_j(t) = (1 - omega) lam_j + omega (S0 + (c_j - u).B)
+// plus the probe term.  The index row is read twice (once per gather); the
+// second read hits L1.  A TMA-staged index tile (as in k_step) measured no
+// faster here and costs 56 KiB of shared memory per block.
+template <typename S, bool GPREV, typename I>
+__device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const S* __restrict__ mu_next,
+                                               S* __restrict__ mu_out, const int32_t* __restrict__ src,
+                                               const AdjParams& ap, const ProbeMap& pm, int store, int64_t x,
+                                               typename Real<S>::type (*neq)[BLOCK]) {
   using R = typename Real<S>::type;
-  __shared__ IdxTiles t;
-  __shared__ R neq[Q][TILE];
-  __shared__ double sh[TILE / 32];
-  const int64_t n = ap.prev.n;
+  const I n = (I)ap.prev.n, sn = (I)ap.prev.sn, xi = (I)x;
   const R omega = R(ap.prev.omega);
   double dtau_local = 0;
-  tile_loop(t, src, n, ap.prev.sn, err, [&](int64_t x, const int32_t* codes, bool ok) {
-    if (!ok || x >= n) return;
-    bool iolet = false;
-    Macro<R> m;
-    {
-      R h[Q];
-      h[0] = ldpop(prev + x);
+  bool iolet = x >= ap.prev.n;
+  Macro<R> m;
+  if (!iolet) {
+    R h[Q];
+    h[0] = ldpop(prev + xi);
 #pragma unroll
-      for (int i = 1; i < Q; ++i) {
-        const int32_t s = codes[(i - 1) * TILE];
-        h[i] = ldpop(prev + (GPREV ? (s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x) : (int64_t)i * n + x));
-        iolet |= s <= -2;
-      }
-      if (iolet) return;  // k_adjoint_iolet
+    for (int i = 1; i < Q; ++i) {
+      const int32_t s = __ldg(src + (I)(i - 1) * sn + xi);
+      h[i] = ldpop(prev + (GPREV ? (s >= 0 ? (I)i * n + (I)s : (I)opp(i) * n + xi) : (I)i * n + xi));
+      iolet |= s <= -2;
+    }
+    if (!iolet) {  // iolet sites: k_adjoint_iolet
       m = moments<R>(h);
       const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
 #pragma unroll
       for (int i = 0; i < Q; ++i) neq[i][threadIdx.x] = h[i] - heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15);
     }
+  }
+  if (!iolet) {
     R lam[Q];
-    lam[0] = ldpop(mu_next + x);
+    lam[0] = ldpop(mu_next + xi);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int32_t s = codes[(i - 1) * TILE];
+      const int32_t s = __ldca(src + (I)(i - 1) * sn + xi);  // a re-read, not held in registers
       // s'_opp(i)(x) is read by x - c_i = x + c_opp(i) in direction opp(i)
-      lam[opp(i)] = ldpop(mu_next + (s >= 0 ? (int64_t)opp(i) * n + s : (int64_t)i * n + x));
+      lam[opp(i)] = ldpop(mu_next + (s >= 0 ? (I)opp(i) * n + (I)s : (I)i * n + xi));
     }
     const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     R S0 = R(0), Lw = R(0), Bx = R(0), By = R(0), Bz = R(0), dt = R(0);
@@ -136,7 +134,7 @@ __global__ void __launch_bounds__(TILE, sizeof(typename Real<S>::type) == 8 ? 1 
     Bx -= R(3) * m.ux * Lw;
     By -= R(3) * m.uy * Lw;
     Bz -= R(3) * m.uz * Lw;
-    dtau_local += (double)(omega * omega * dt);
+    dtau_local = (double)(omega * omega * dt);
     if (store) {
       // mu_j = (1-omega) lam_j + omega (S0 + (c_j - u).B) + pg (c_j - u).axis
       //      = (1-omega) lam_j + T0 + c_j.E
@@ -150,12 +148,35 @@ __global__ void __launch_bounds__(TILE, sizeof(typename Real<S>::type) == 8 ? 1 
         if (cx(j)) v += cx(j) > 0 ? Ex : -Ex;
         if (cy(j)) v += cy(j) > 0 ? Ey : -Ey;
         if (cz(j)) v += cz(j) > 0 ? Ez : -Ez;
-        mu_out[(int64_t)j * n + x] = from_real<S>(v);
+        mu_out[(I)j * n + xi] = from_real<S>(v);
       }
     }
-  });
-  const double bs = block_sum(dtau_local, sh);
-  if (threadIdx.x == 0) dtau_part[blockIdx.x] += bs;
+  }
+  return dtau_local;
+}
+
+// Warp sums for the iolet-site reverse kernel: xor butterflies (5 shuffles a
+// sum).  Each level adds the same two partials on both lanes of a pair, so
+// every lane ends with identical bits.  Lanes 19..31 must hold 0.
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  return v;
+}
+// (sum v, sum v c) with lane i holding v for direction i
+template <typename R>
+__device__ __forceinline__ void warp_moment_sums(R v, int i, R* d, R* jx, R* jy, R* jz) {
+  R a = v, x = k_cx[i] ? (k_cx[i] > 0 ? v : -v) : R(0), y = k_cy[i] ? (k_cy[i] > 0 ? v : -v) : R(0),
+    z = k_cz[i] ? (k_cz[i] > 0 ? v : -v) : R(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(FULL_MASK, a, o);
+    x += __shfl_xor_sync(FULL_MASK, x, o);
+    y += __shfl_xor_sync(FULL_MASK, y, o);
+    z += __shfl_xor_sync(FULL_MASK, z, o);
+  }
+  *d = a; *jx = x; *jy = y; *jz = z;
 }
 
 // Reverse step of the sites with iolet links: one warp per site, lane i =
@@ -165,18 +186,16 @@ __global__ void __launch_bounds__(TILE, sizeof(typename Real<S>::type) == 8 ? 1 
 // s'(t) at the site), applies the collision transpose, and accumulates the
 // per-link amplitude derivatives (each link record belongs to one lane).
 template <typename S, bool GPREV>
-__global__ void __launch_bounds__(256) k_adjoint_iolet(const S* __restrict__ prev, const S* __restrict__ cur,
-                                                       const S* __restrict__ mu_next, S* __restrict__ mu_out,
-                                                       const int32_t* __restrict__ src,
-                                                       const LinkRec* __restrict__ links,
-                                                       const double* __restrict__ amp, const AdjParams ap,
-                                                       const ProbeMap pm, const int32_t* __restrict__ sites,
-                                                       int64_t nsites, double* __restrict__ dtau_part,
-                                                       double* __restrict__ dlink, int store) {
+__device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev, const S* __restrict__ cur,
+                                                     const S* __restrict__ mu_next, S* __restrict__ mu_out,
+                                                     const int32_t* __restrict__ src,
+                                                     const LinkRec* __restrict__ links,
+                                                     const double* __restrict__ amp, const AdjParams& ap,
+                                                     const ProbeMap& pm, const int32_t* __restrict__ sites,
+                                                     int64_t nsites, double* __restrict__ dlink, int store,
+                                                     int64_t w) {
   using R = typename Real<S>::type;
-  __shared__ double sh[8];
   const StepParams& p = ap.prev;
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int i = threadIdx.x & 31;
   const bool dir = i < Q;
   double dtau_local = 0;
@@ -192,7 +211,7 @@ __global__ void __launch_bounds__(256) k_adjoint_iolet(const S* __restrict__ pre
         own = ldpop(prev + (int64_t)i * n + x);
       }
       R d, jx, jy, jz;
-      lane_moment_sums<R>(own, R(1), &d, &jx, &jy, &jz);
+      warp_moment_sums<R>(own, i, &d, &jx, &jy, &jz);
       const R rp = R(1) + d;
       const R ux = jx / rp, uy = jy / rp, uz = jz / rp;
       if (code <= -2) {
@@ -210,7 +229,7 @@ __global__ void __launch_bounds__(256) k_adjoint_iolet(const S* __restrict__ pre
     // boundary transposes of G_t (moments of s'(t) at x)
     const R c = dir ? ldpop(cur + (int64_t)i * n + x) : R(0);
     R d, jx, jy, jz;
-    lane_moment_sums<R>(c, R(1), &d, &jx, &jy, &jz);
+    warp_moment_sums<R>(c, i, &d, &jx, &jy, &jz);
     const R rho_s = R(1) + d;
     const R usx = jx / rho_s, usy = jy / rho_s, usz = jz / rho_s;
     R gs = R(0), gx = R(0), gy = R(0), gz = R(0);
@@ -251,22 +270,31 @@ __global__ void __launch_bounds__(256) k_adjoint_iolet(const S* __restrict__ pre
         gz = vz;
       }
     }
-    const R gsum = lane_sum<R>(gs), gux = lane_sum<R>(gx), guy = lane_sum<R>(gy), guz = lane_sum<R>(gz);
+    const R gsum = warp_sum<R>(gs), gux = warp_sum<R>(gx), guy = warp_sum<R>(gy), guz = warp_sum<R>(gz);
     // lam_i, with d u_s / d s'_j = (c_j - u_s) / rho_s and d rho_s / d s'_j = 1
     R lam = __shfl_sync(FULL_MASK, lo, lane_opp(i < Q ? i : 0));
     lam += gsum + ((R(k_cx[i]) - usx) * gux + (R(k_cy[i]) - usy) * guy + (R(k_cz[i]) - usz) * guz) / rho_s;
     if (!dir) lam = R(0);
     // collision transpose at f(t) = h
-    const Macro<R> m = lane_moments<R>(h);
+    Macro<R> m;
+    {
+      R jx, jy, jz;
+      warp_moment_sums<R>(h, i, &m.drho, &jx, &jy, &jz);
+      m.rho = R(1) + m.drho;
+      const R inv = R(1) / m.rho;
+      m.ux = jx * inv;
+      m.uy = jy * inv;
+      m.uz = jz * inv;
+    }
     const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     const R omega = R(p.omega);
     const R cu = lane_cdotu<R>(i, m.ux, m.uy, m.uz);
     const R wi = lane_w<R>(i);
     const R b = lam * wi * (R(3) + R(9) * cu);
-    const R S0 = lane_sum<R>(lam * wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15));
-    const R Lw = lane_sum<R>(lam * wi);
-    R Bx = lane_sum<R>(b * R(k_cx[i])), By = lane_sum<R>(b * R(k_cy[i])), Bz = lane_sum<R>(b * R(k_cz[i]));
-    const R dt = lane_sum<R>(dir ? lam * (h - lane_heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15)) : R(0));
+    const R S0 = warp_sum<R>(lam * wi * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15));
+    const R Lw = warp_sum<R>(lam * wi);
+    R Bx = warp_sum<R>(b * R(k_cx[i])), By = warp_sum<R>(b * R(k_cy[i])), Bz = warp_sum<R>(b * R(k_cz[i]));
+    const R dt = warp_sum<R>(dir ? lam * (h - lane_heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15)) : R(0));
     Bx -= R(3) * m.ux * Lw;
     By -= R(3) * m.uy * Lw;
     Bz -= R(3) * m.uz * Lw;
@@ -280,8 +308,37 @@ __global__ void __launch_bounds__(256) k_adjoint_iolet(const S* __restrict__ pre
       mu_out[(int64_t)i * n + x] = from_real<S>(v);
     }
   }
-  const double bs = block_sum(dtau_local, sh);
-  if (threadIdx.x == 0) dtau_part[blockIdx.x] += bs;
+  return dtau_local;
+}
+
+// One reverse step in one launch.  Every stride-th block (the first
+// n_iolet_blocks of them) takes eight iolet sites, a warp each; the others
+// take 256 bulk sites, a thread each.  Spreading the short, latency-bound
+// iolet blocks through the grid lets them run beside the bulk blocks instead
+// of ahead of them.  Block b's dJ/dtau partial goes to part[b] (fixed order).
+// I is the element-offset type: 32-bit whenever 19 x the row stride fits,
+// which keeps the 38 gather addresses from spilling.
+template <typename S, bool GPREV, typename I>
+__global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2 : 4)
+    k_adjoint(const S* __restrict__ prev, const S* __restrict__ cur, const S* __restrict__ mu_next,
+              S* __restrict__ mu_out, const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
+              const double* __restrict__ amp, const AdjParams ap, const ProbeMap pm,
+              const int32_t* __restrict__ sites, int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
+              double* __restrict__ part, double* __restrict__ dlink, int store) {
+  using R = typename Real<S>::type;
+  __shared__ R neq[Q][BLOCK];
+  __shared__ double sh[BLOCK / 32];
+  const unsigned b = blockIdx.x, j = b / stride;
+  double d;
+  if (b % stride == 0 && j < n_iolet_blocks) {
+    d = adjoint_iolet_site<S, GPREV>(prev, cur, mu_next, mu_out, src, links, amp, ap, pm, sites, nsites, dlink,
+                                     store, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
+  } else {
+    const unsigned k = b - min(n_iolet_blocks, j + 1);  // bulk tile: blocks before b that are not iolet blocks
+    d = adjoint_site<S, GPREV, I>(prev, mu_next, mu_out, src, ap, pm, store, (int64_t)k * BLOCK + threadIdx.x, neq);
+  }
+  const double bs = block_sum(d, sh);
+  if (threadIdx.x == 0) part[b] += bs;
 }
 
 // Objective term at time t for every probe: accumulate (u.axis - target)^2 / N.
@@ -345,24 +402,6 @@ __global__ void k_adj_finish(const double* __restrict__ jp, int64_t np, const do
 }
 
 
-// Persistent grid of the bulk reverse kernel (resident CTAs x SMs, capped by
-// the tile count); its per-CTA partials occupy the first slots of dtau_part.
-template <typename K>
-unsigned adj_grid(const hlb_solver* h, K kernel) {
-  static int cache[64] = {0};
-  const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
-  if (!cache[dev]) {
-    int sms = 0, occ = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // prefer the largest shared-memory carveout: these kernels stage index tiles
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TILE, 0);
-    cache[dev] = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
-  }
-  const int64_t ntiles = (h->n + TILE - 1) / TILE;
-  return (unsigned)(ntiles < cache[dev] ? ntiles : cache[dev]);
-}
-
 template <typename S>
 cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, const void* cur, const void* mu_next,
                            void* mu_out, int64_t tb_prev, int64_t tb_cur, const ProbeMap& pm, double* dtau_part,
@@ -372,25 +411,15 @@ cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, co
   StepParams pc = h->params(tb_cur);
   for (int k = 0; k < MAX_IOLETS; ++k) ap.val_cur[k] = k < h->n_iolets ? pc.io[k].val : 0.0;
   const int st_ = store ? 1 : 0;
-  double* part_i = dtau_part + grid_for(h->n);  // partials of the iolet-site kernel
   const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // one warp per iolet site
-  if (gprev) {
-    k_adjoint<S, true><<<adj_grid(h, k_adjoint<S, true>), TILE, 0, st>>>((const S*)prev, (const S*)mu_next,
-                                                                          (S*)mu_out, h->d_src, ap, pm, dtau_part,
-                                                                          st_, h->d_err);
-    if (gi)
-      k_adjoint_iolet<S, true><<<gi, 256, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
-                                                   h->d_src, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
-                                                   h->n_iolet_sites, part_i, dlink, st_);
-  } else {
-    k_adjoint<S, false><<<adj_grid(h, k_adjoint<S, false>), TILE, 0, st>>>((const S*)prev, (const S*)mu_next,
-                                                                            (S*)mu_out, h->d_src, ap, pm, dtau_part,
-                                                                            st_, h->d_err);
-    if (gi)
-      k_adjoint_iolet<S, false><<<gi, 256, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out,
-                                                    h->d_src, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
-                                                    h->n_iolet_sites, part_i, dlink, st_);
-  }
+  const unsigned grid = gi + grid_for(h->n);
+  const unsigned stride = gi ? grid / gi : 1;  // gi * stride <= grid
+  const bool off32 = (uint64_t)Q * (uint64_t)h->sn <= 0xffffffffull;
+  auto kernel = gprev ? (off32 ? k_adjoint<S, true, uint32_t> : k_adjoint<S, true, int64_t>)
+                      : (off32 ? k_adjoint<S, false, uint32_t> : k_adjoint<S, false, int64_t>);
+  kernel<<<grid, BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src, h->d_links,
+                                 h->d_amp, ap, pm, h->d_iolet_sites, h->n_iolet_sites, gi, stride, dtau_part, dlink,
+                                 st_);
   return cudaGetLastError();
 }
 
