@@ -111,12 +111,19 @@ typedef struct {
  *   faster measured scheme.
  * ladd_rho_one: 1 = use rho = 1 in the Ladd correction instead of the
  *   site's density (the paper does not say which density).
- * ghost_full_u: 1 = pressure-iolet ghost velocity u instead of (u.n) n. */
+ * ghost_full_u: 1 = pressure-iolet ghost velocity u instead of (u.n) n.
+ * wide_offsets: 1 = always address populations and the index table with
+ *   64-bit element offsets.  The step and adjoint kernels use 32-bit offsets
+ *   whenever 19 x the index row stride fits in 32 bits (up to about 226M
+ *   sites) and 64-bit ones above; this flag selects the 64-bit kernels at
+ *   any size, so that they can be checked on small lattices.  Results are
+ *   identical either way. */
 typedef struct {
   int32_t precision;
   int32_t scheme;
   int32_t ladd_rho_one;
   int32_t ghost_full_u;
+  int32_t wide_offsets;
 } hlb_options;
 
 /* Time-dependent scalar w(t):

@@ -14,8 +14,10 @@
 //   dJ/da_g = sum_t mu(t+1) . dG_t/da_g
 // G_t^T is itself a gather: s'_i(x) is read by the site x + c_i, whose
 // index is src[opp(i)][x], or (boundary link) by x itself in direction
-// opp(i).  One kernel per reverse step reads the index table once and
-// gathers both mu(t+1) and s'(t-1) (to recompute f(t)).
+// opp(i).  One kernel per reverse step reads the index table and gathers
+// both mu(t+1) and s'(t-1) (to recompute f(t)).  J itself is summed in the
+// reverse sweep too, where f(t)'s moments are at hand, so the forward sweep
+// runs the plain step kernels and nothing else.
 #include <math.h>
 
 #include <algorithm>
@@ -31,28 +33,33 @@ constexpr int BLOCK = 256;
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
 // Probe sites as a bit mask over sites plus per-32-site prefix counts: site
-// x is a probe when bit x of mask is set, and its target is
-// target[base[x / 32] + popcount(mask bits of its word below x)].  Lets the
-// reverse kernels add dJ/df(t) at the probes without a separate launch.
+// x is probe k when bit x of mask is set, k = base[x / 32] + popcount(mask
+// bits of its word below x).  Lets the reverse kernels evaluate the
+// objective and add dJ/df(t) at the probes without launches of their own.
 struct ProbeMap {
   const uint32_t* mask;
   const int32_t* base;
   const double* target;  // ordered by site
+  double* jp;            // per-probe objective accumulators, ordered by site
   double ax, ay, az;
-  double g2;             // 2 / N
+  double inv_n;          // 1 / N
 };
 
-// dJ/df_j(t) at site x = pg (c_j . axis - u_ax); pg = 0 off the probes.
+// At a probe, with d = u(t).axis - target: J gains d^2 / N (when add_j) and
+// dJ/df_j(t) = pg (c_j . axis - u_ax) with pg = 2 d / (N rho).  pg = 0 off
+// the probes.
 template <typename R>
-__device__ __forceinline__ R probe_coef(const ProbeMap& pm, int64_t x, const Macro<R>& m, R* uax) {
+__device__ __forceinline__ R probe_term(const ProbeMap& pm, int64_t x, const Macro<R>& m, R* uax, bool add_j) {
   const uint32_t word = pm.mask[x >> 5];
   const uint32_t bit = (uint32_t)(x & 31);
   *uax = R(0);
   if (!((word >> bit) & 1u)) return R(0);
   const int k = pm.base[x >> 5] + __popc(word & ((1u << bit) - 1u));
-  const R ua = m.ux * R(pm.ax) + m.uy * R(pm.ay) + m.uz * R(pm.az);
-  *uax = ua;
-  return R(pm.g2) * (ua - R(pm.target[k])) / m.rho;
+  const double ua = (double)m.ux * pm.ax + (double)m.uy * pm.ay + (double)m.uz * pm.az;
+  const double d = ua - pm.target[k];
+  if (add_j) pm.jp[k] += d * d * pm.inv_n;
+  *uax = R(ua);
+  return R(2.0 * pm.inv_n * d) / m.rho;
 }
 
 struct AdjParams {
@@ -139,7 +146,7 @@ __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const
       // mu_j = (1-omega) lam_j + omega (S0 + (c_j - u).B) + pg (c_j - u).axis
       //      = (1-omega) lam_j + T0 + c_j.E
       R uax;
-      const R pg = probe_coef<R>(pm, x, m, &uax);
+      const R pg = probe_term<R>(pm, x, m, &uax, true);
       const R Ex = omega * Bx + pg * R(pm.ax), Ey = omega * By + pg * R(pm.ay), Ez = omega * Bz + pg * R(pm.az);
       const R T0 = omega * (S0 - m.ux * Bx - m.uy * By - m.uz * Bz) - pg * uax;
 #pragma unroll
@@ -301,7 +308,7 @@ __device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev,
     if (i == 0) dtau_local = (double)(omega * omega * dt);
     if (store && dir) {
       R uax;
-      const R pg = probe_coef<R>(pm, x, m, &uax);
+      const R pg = probe_term<R>(pm, x, m, &uax, i == 0);
       R v = (R(1) - omega) * lam +
             omega * (S0 + (R(k_cx[i]) - m.ux) * Bx + (R(k_cy[i]) - m.uy) * By + (R(k_cz[i]) - m.uz) * Bz);
       v += pg * (R(k_cx[i]) * R(pm.ax) + R(k_cy[i]) * R(pm.ay) + R(k_cz[i]) * R(pm.az) - uax);
@@ -341,31 +348,15 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2
   if (threadIdx.x == 0) part[b] += bs;
 }
 
-// Objective term at time t for every probe: accumulate (u.axis - target)^2 / N.
-template <typename S, int MODE>
-__global__ void k_probe_obj(const S* __restrict__ fin, const int32_t* __restrict__ src,
-                            const LinkRec* __restrict__ links, const double* __restrict__ amp, const StepParams p,
-                            const int64_t* __restrict__ sites, const double* __restrict__ target, double ax,
-                            double ay, double az, double invN, int64_t np, double* __restrict__ jp) {
-  using R = typename Real<S>::type;
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= np) return;
-  const int64_t x = sites[q];
-  R h[Q];
-  load_state<S, MODE>(fin, src, links, amp, p, x, h);
-  const Macro<R> m = moments<R>(h);
-  const double ua = (double)m.ux * ax + (double)m.uy * ay + (double)m.uz * az;
-  const double d = ua - target[q];
-  jp[q] += d * d * invN;
-}
-
-// Objective derivative at time t added to mu(t) at the probes:
-// dJ/df_j = (2/N) (u.axis - target) (c_j.axis - u.axis) / rho.
+// The objective's last term, t = N: J gains (u.axis - target)^2 / N and
+// mu(N) = dJ/df(N), dJ/df_j = (2/N) (u.axis - target) (c_j.axis - u.axis) / rho
+// (added to mu, which holds zeros).
 template <typename S, int MODE>
 __global__ void k_probe_adj(const S* __restrict__ fin, const int32_t* __restrict__ src,
                             const LinkRec* __restrict__ links, const double* __restrict__ amp, const StepParams p,
                             const int64_t* __restrict__ sites, const double* __restrict__ target, double ax,
-                            double ay, double az, double invN, int64_t np, S* __restrict__ mu) {
+                            double ay, double az, double invN, int64_t np, S* __restrict__ mu,
+                            double* __restrict__ jp) {
   using R = typename Real<S>::type;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= np) return;
@@ -373,8 +364,11 @@ __global__ void k_probe_adj(const S* __restrict__ fin, const int32_t* __restrict
   R h[Q];
   load_state<S, MODE>(fin, src, links, amp, p, x, h);
   const Macro<R> m = moments<R>(h);
-  const R ua = m.ux * R(ax) + m.uy * R(ay) + m.uz * R(az);
-  const R g = R(2.0 * invN) * (ua - R(target[q])) / m.rho;
+  const double uad = (double)m.ux * ax + (double)m.uy * ay + (double)m.uz * az;
+  const double dd = uad - target[q];
+  jp[q] += dd * dd * invN;
+  const R ua = R(uad);
+  const R g = R(2.0 * invN * dd) / m.rho;
 #pragma unroll
   for (int j = 0; j < Q; ++j) {
     const R cj = R(cx(j)) * R(ax) + R(cy(j)) * R(ay) + R(cz(j)) * R(az);
@@ -414,7 +408,7 @@ cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, co
   const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // one warp per iolet site
   const unsigned grid = gi + grid_for(h->n);
   const unsigned stride = gi ? grid / gi : 1;  // gi * stride <= grid
-  const bool off32 = (uint64_t)Q * (uint64_t)h->sn <= 0xffffffffull;
+  const bool off32 = h->off32;
   auto kernel = gprev ? (off32 ? k_adjoint<S, true, uint32_t> : k_adjoint<S, true, int64_t>)
                       : (off32 ? k_adjoint<S, false, uint32_t> : k_adjoint<S, false, int64_t>);
   kernel<<<grid, BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src, h->d_links,
@@ -438,26 +432,14 @@ struct Probe {
   }
 
 template <typename S>
-cudaError_t launch_probe_obj(const hlb_solver* h, const void* fin, int mode, int64_t tb, const Probe& pr, double* jp,
-                             cudaStream_t st) {
-  if (pr.np == 0) return cudaSuccess;
-  StepParams p = h->params(tb);
-  const unsigned g = (unsigned)((pr.np + 127) / 128);
-  PROBE_MODE_SWITCH(mode, (k_probe_obj<S, M><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p,
-                                                                 pr.sites, pr.target, pr.ax, pr.ay, pr.az, pr.invN,
-                                                                 pr.np, jp)));
-  return cudaGetLastError();
-}
-
-template <typename S>
 cudaError_t launch_probe_adj(const hlb_solver* h, const void* fin, int mode, int64_t tb, const Probe& pr, void* mu,
-                             cudaStream_t st) {
+                             double* jp, cudaStream_t st) {
   if (pr.np == 0) return cudaSuccess;
   StepParams p = h->params(tb);
   const unsigned g = (unsigned)((pr.np + 127) / 128);
   PROBE_MODE_SWITCH(mode, (k_probe_adj<S, M><<<g, 128, 0, st>>>((const S*)fin, h->d_src, h->d_links, h->d_amp, p,
                                                                  pr.sites, pr.target, pr.ax, pr.ay, pr.az, pr.invN,
-                                                                 pr.np, (S*)mu)));
+                                                                 pr.np, (S*)mu, jp)));
   return cudaGetLastError();
 }
 
@@ -552,7 +534,7 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   }
   TRY(cudaMemcpyAsync(d_mask, mask.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, st));
   TRY(cudaMemcpyAsync(d_base, base.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
-  const ProbeMap pm{d_mask, d_base, d_target, obj->axis[0], obj->axis[1], obj->axis[2], 2.0 / (double)N};
+  const ProbeMap pm{d_mask, d_base, d_target, jp, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N};
   TRY(cudaMemcpyAsync(gbegin, h->group_link_begin.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, st));
   Probe pr{d_sites, d_target, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N, np};
 
@@ -565,7 +547,6 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   for (int64_t s = 0; s < N; ++s) {
     TRY(hlb_launch_aa(h, W, swapped, t0 + s, st));
     swapped = !swapped;
-    TRY(launch_probe_obj<S>(h, W, swapped ? HLB_READ_GATHER_AA : HLB_READ_LOCAL, t0 + s, pr, jp, st));
     if (!swapped && (s + 1) % K == 0 && (s + 1) / K < nck)
       TRY(cudaMemcpyAsync(ck((s + 1) / K), W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
   }
@@ -585,7 +566,7 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   // pull kernels from its checkpoint, then sweep it backwards ----
   int a = 0;  // mu[a] holds mu(t+1)
   TRY(cudaMemsetAsync(mu[a], 0, h->state_bytes(), st));
-  TRY(launch_probe_adj<S>(h, fin_state, fin_mode, t0 + N - 1, pr, mu[a], st));
+  TRY(launch_probe_adj<S>(h, fin_state, fin_mode, t0 + N - 1, pr, mu[a], jp, st));
   for (int64_t c = nck - 1; c >= 0; --c) {
     const int64_t sb = c * K, se = std::min<int64_t>(N, (c + 1) * K);
     const void* rin = ck(c);

@@ -41,7 +41,7 @@ int hlb_check_device_error(hlb_solver* h) {
   if (flag) return hlb_fail(HLB_ERR_CUDA, "a device wait for a staged index tile timed out; results are invalid");
   return HLB_OK;
 }
-extern "C" int hlb_version(void) { return 10000; }
+extern "C" int hlb_version(void) { return 10100; }
 
 // ---------------------------------------------------------------------------
 // waveforms
@@ -242,6 +242,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->scheme = resolve_scheme(o->scheme);
   h->ladd_rho_one = o->ladd_rho_one ? 1 : 0;
   h->ghost_full_u = o->ghost_full_u ? 1 : 0;
+  h->off32 = !o->wide_offsets && (uint64_t)Q * (uint64_t)h->sn <= 0xffffffffull;
   h->stream = (cudaStream_t)stream;
   h->device = attr.device;
   h->has_normals = L->wall_normal != nullptr;

@@ -83,14 +83,11 @@ __global__ void __launch_bounds__(TILE, 5) k_step(const S* __restrict__ fin, S* 
 // sums in direction order so that every value equals the per-thread
 // read-back path (iolet_fixup) bit for bit.
 template <typename S>
-__global__ void __launch_bounds__(256) k_step_iolet(const S* __restrict__ fin, S* __restrict__ fout,
-                                                    const int32_t* __restrict__ src,
-                                                    const LinkRec* __restrict__ links,
-                                                    const double* __restrict__ amp,
-                                                    const int32_t* __restrict__ sites, int64_t nsites,
-                                                    const StepParams p) {
+__device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __restrict__ fout,
+                                                const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
+                                                const double* __restrict__ amp, const int32_t* __restrict__ sites,
+                                                int64_t nsites, const StepParams& p, int64_t w) {
   using R = typename Real<S>::type;
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (w >= nsites) return;  // uniform across the warp
   const int i = threadIdx.x & 31;
   const bool dir = i < Q;
@@ -116,6 +113,54 @@ __global__ void __launch_bounds__(256) k_step_iolet(const S* __restrict__ fin, S
     h += R(p.omega) * (lane_heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15) - h);
     stpop<S>(fout + (int64_t)i * n + x, h);
   }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_step_iolet(const S* __restrict__ fin, S* __restrict__ fout,
+                                                    const int32_t* __restrict__ src,
+                                                    const LinkRec* __restrict__ links,
+                                                    const double* __restrict__ amp,
+                                                    const int32_t* __restrict__ sites, int64_t nsites,
+                                                    const StepParams p) {
+  step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p,
+                     ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+}
+
+// Pull A-B step in one launch with 32-bit element offsets (19 x the row
+// stride fits in 32 bits) and no staged index tiles.  Every stride-th block
+// (the first n_iolet_blocks of them) takes eight iolet sites, a warp each,
+// exactly as k_step_iolet; the others take 256 bulk sites, a thread each.
+// The iolet blocks, spread through the grid, run beside the bulk blocks
+// instead of after them.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 5) k_step32(const S* __restrict__ fin, S* __restrict__ fout,
+                                                  const int32_t* __restrict__ src,
+                                                  const LinkRec* __restrict__ links,
+                                                  const double* __restrict__ amp,
+                                                  const int32_t* __restrict__ sites, int64_t nsites,
+                                                  unsigned n_iolet_blocks, unsigned stride, const StepParams p) {
+  using R = typename Real<S>::type;
+  const unsigned b = blockIdx.x, j = b / stride;
+  if (b % stride == 0 && j < n_iolet_blocks) {
+    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
+    return;
+  }
+  const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
+  const uint32_t x = (b - min(n_iolet_blocks, j + 1)) * BLOCK + threadIdx.x;
+  if (x >= n) return;
+  R h[Q];
+  h[0] = ldpop(fin + x);
+  bool iolet = false;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int32_t s = ldidx(src + (uint32_t)(i - 1) * sn + x);
+    h[i] = ldpop(fin + (s >= 0 ? (uint32_t)i * n + (uint32_t)s : (uint32_t)opp(i) * n + x));
+    iolet |= s <= -2;
+  }
+  if (iolet) return;
+  collide<R>(h, R(p.omega));
+#pragma unroll
+  for (int i = 0; i < Q; ++i) stpop<S>(fout + (uint32_t)i * n + x, h[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,6 +300,31 @@ __global__ void __launch_bounds__(BLOCK, 4) k_aa_odd(S* A, const int32_t* __rest
   stpop<S>(A + x, h[0]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) stpop<S>(A + aa_addr(i, __ldg(src + (int64_t)(i - 1) * sn + x), n, x), h[opp(i)]);
+}
+
+// The same step with 32-bit element offsets (19 x the row stride fits in 32
+// bits): the 18 slot offsets are computed once and held in registers for the
+// stores, so the index row is read only once.  Five resident blocks per SM
+// (51 registers, a few bytes of spill in FP32) measured fastest.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 5) k_aa_odd32(S* A, const int32_t* __restrict__ src, const StepParams p) {
+  using R = typename Real<S>::type;
+  const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
+  const uint32_t x = blockIdx.x * BLOCK + threadIdx.x;
+  if (x >= n) return;
+  uint32_t off[Q];
+  R h[Q];
+  h[0] = to_real(A[x]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const int32_t s = __ldg(src + (uint32_t)(i - 1) * sn + x);
+    off[i] = s >= 0 ? (uint32_t)opp(i) * n + (uint32_t)s : (uint32_t)i * n + x;
+    h[i] = to_real(A[off[i]]);
+  }
+  collide<R>(h, R(p.omega));
+  stpop<S>(A + x, h[0]);
+#pragma unroll
+  for (int i = 1; i < Q; ++i) stpop<S>(A + off[i], h[opp(i)]);
 }
 
 // ---------------------------------------------------------------------------
@@ -510,7 +580,12 @@ struct StepOp {
   static cudaError_t run(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
                          cudaStream_t s) {
     StepParams p = h->params(tb);
-    if (gather) {
+    if (gather && h->off32) {
+      const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // 8 warps (sites) per block
+      const unsigned grid = gi + grid_for(h->n);
+      k_step32<S><<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+                                         h->n_iolet_sites, gi, gi ? grid / gi : 1, p);
+    } else if (gather) {
       k_step<S><<<persistent_grid(h, k_step<S>), TILE, 0, s>>>((const S*)fin, (S*)fout, h->d_src, p, h->d_err);
       if (h->n_iolet_sites > 0)
         k_step_iolet<S><<<(unsigned)((h->n_iolet_sites + 7) / 8), 256, 0, s>>>(
@@ -546,7 +621,9 @@ struct AAOp {
   static cudaError_t run(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
     StepParams p = h->params(t);
     if (odd)
-      if (h->sn == h->n)
+      if (h->off32)
+        k_aa_odd32<S><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
+      else if (h->sn == h->n)
         k_aa_odd<S, true><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
       else
         k_aa_odd<S, false><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);

@@ -39,6 +39,7 @@ struct hlb_solver {
   int32_t scheme = HLB_PULL_AB;
   int32_t ladd_rho_one = 0;
   int32_t ghost_full_u = 0;
+  bool off32 = true;  // 32-bit element offsets in the step/adjoint kernels (19 x sn fits)
 
   // state
   cudaStream_t stream = nullptr;

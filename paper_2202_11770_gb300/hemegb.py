@@ -52,7 +52,7 @@ class hlb_lattice(C.Structure):
 
 class hlb_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("scheme", C.c_int32), ("ladd_rho_one", C.c_int32),
-                ("ghost_full_u", C.c_int32)]
+                ("ghost_full_u", C.c_int32), ("wide_offsets", C.c_int32)]
 
 
 class hlb_waveform(C.Structure):
@@ -219,7 +219,7 @@ class Solver:
     """
 
     def __init__(self, lattice, tau=1.0, precision="fp32", scheme="auto", ladd_rho_one=False,
-                 ghost_full_u=False, use_normals=True, stream=None):
+                 ghost_full_u=False, use_normals=True, stream=None, wide_offsets=False):
         torch = _torch()
         lib = library()
         self._torch = torch
@@ -246,7 +246,7 @@ class Solver:
         self._ios = ios
         scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self._opt = hlb_options(precision=self.precision, scheme=scheme, ladd_rho_one=int(ladd_rho_one),
-                                ghost_full_u=int(ghost_full_u))
+                                ghost_full_u=int(ghost_full_u), wide_offsets=int(wide_offsets))
         nbytes = hlb_workspace_bytes(self._lat, self._opt)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self.workspace.data_ptr()

@@ -26,8 +26,8 @@ def _setup(x, lat, amps):
     x.init_equilibrium()
 
 
-@pytest.mark.parametrize("opts", [(False, False), (True, True)])
-def test_fp64_adjoint_equals_oracle(opts):
+@pytest.mark.parametrize("opts,wide", [((False, False), False), ((True, True), False), ((False, False), True)])
+def test_fp64_adjoint_equals_oracle(opts, wide):
     lat = geo.tree(1, 7, root_radius=4.0, length_ratio=5.0, n_sectors=2, n_rings=2)
     N, tau = 40, 0.7
     probe = np.nonzero(lat.xyz[:, 2] == int(lat.info["root_length"] // 2))[0]
@@ -37,7 +37,8 @@ def test_fp64_adjoint_equals_oracle(opts):
     o = oracle.Oracle(lat, tau, *opts)
     _setup(o, lat, amps)
     J_o, dtau_o, damp_o = o.adjoint(N, probe, target, [0, 0, 1])
-    s = hemegb.Solver(lat, tau=tau, precision="fp64", ladd_rho_one=opts[0], ghost_full_u=opts[1])
+    s = hemegb.Solver(lat, tau=tau, precision="fp64", ladd_rho_one=opts[0], ghost_full_u=opts[1],
+                      wide_offsets=wide)
     _setup(s, lat, amps)
     J, dtau, damp = s.adjoint(N, probe, target, [0, 0, 1])
     assert s.t == N

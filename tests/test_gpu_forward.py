@@ -47,9 +47,11 @@ def pipe():
     return geo.pipe(8.0, 64)
 
 
+@pytest.mark.parametrize("wide", [False, True], ids=["off32", "off64"])
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_pipe_fp32_1000_steps(pipe, scheme):
-    s, o = _both(pipe, 0.8, _pipe_bc, scheme=scheme)
+def test_pipe_fp32_1000_steps(pipe, scheme, wide):
+    """wide: the 64-bit-offset kernels, which lattices above ~226M sites use."""
+    s, o = _both(pipe, 0.8, _pipe_bc, scheme=scheme, wide_offsets=wide)
     s.step(1000)
     o.step(1000)
     rho, u, wss = s.macros()
@@ -152,8 +154,9 @@ def test_isolated_site_and_small_lattices(d3q19, scheme):
         assert np.abs(rho - rho_o).max() < 1e-6
 
 
+@pytest.mark.parametrize("wide", [False, True], ids=["off32", "off64"])
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_tree_several_tiles_fp32(scheme):
+def test_tree_several_tiles_fp32(scheme, wide):
     lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0)
     assert lat.n % 256
 
@@ -161,7 +164,7 @@ def test_tree_several_tiles_fp32(scheme):
         x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 200.0})
         for k in range(1, len(lat.iolets)):
             x.set_pressure(k, 1.0)
-    s, o = _both(lat, 0.55, bc, scheme=scheme)
+    s, o = _both(lat, 0.55, bc, scheme=scheme, wide_offsets=wide)
     s.step(301)
     o.step(301)
     _, u, wss = s.macros()
@@ -256,9 +259,10 @@ def _half_ulp(v, prec):
     return 0.5 * 2.0 ** (e - mant)
 
 
-def _one_step_within_rounding(lat, tau, bc, prec, scheme, w, warm=5):
-    """Step the 16-bit solver `warm` steps, then compare one more step with
-    the oracle's FP64 step from the same (exactly representable) state.
+def _one_step_within_rounding(lat, tau, bc, prec, scheme, w, warm=5, wide=False, checks=2):
+    """Step the 16-bit solver `warm` steps, then compare each of the next
+    `checks` steps with the oracle's FP64 step from the same (exactly
+    representable) state; two checks cover both AA parities.
 
     Tight entries: a stored value is the FP64 result rounded to the 16-bit
     format, up to the FP32 collision arithmetic (delta) before the rounding.
@@ -270,22 +274,12 @@ def _one_step_within_rounding(lat, tau, bc, prec, scheme, w, warm=5):
     sum |c_j| < 24) and the equilibrium's sensitivity (w_i rho |d feq/d u|
     < 0.3, and < 7 w_i per unit of input in the collision) that is below 16
     such half-ulps on the result."""
-    s = hemegb.Solver(lat, tau=tau, precision=prec, scheme=scheme)
+    s = hemegb.Solver(lat, tau=tau, precision=prec, scheme=scheme, wide_offsets=wide)
     bc(s)
     s.init_equilibrium()
     s.step(warm)
-    h5, t5 = s.state()
-    s.step(1)
-    h6, _ = s.state()
     o = oracle.Oracle(lat, tau=tau)
     bc(o)
-    o.set_state((_stored_to_f64(h5, prec) + w[:, None]).T, t5)
-    o.step(1)
-    ref = o.state().T - w[:, None]
-    got = _stored_to_f64(h6, prec)
-    delta = 5e-8
-    bound = _half_ulp(np.abs(ref) + delta, prec) + delta
-
     n = lat.n
     src = lat.src
     iolet_site = (src <= -2).any(axis=0)
@@ -293,23 +287,35 @@ def _one_step_within_rounding(lat, tau, bc, prec, scheme, w, warm=5):
     loose = np.empty((19, n), bool)
     loose[0] = iolet_site
     loose[1:] = iolet_site[y] | (src <= -2)
-    site_max = np.abs(ref).max(axis=0)
-    mag = np.maximum(site_max[None, :], np.concatenate([site_max[None, :], site_max[y]]))
-    bound = np.where(loose, bound + 16 * _half_ulp(mag, prec), bound)
     assert loose.mean() < 0.05
-    excess = np.abs(got - ref) - bound
-    k = np.unravel_index(excess.argmax(), excess.shape)
-    assert excess.max() <= 0.0, f"worst excess {excess.max():.3e} at {k} (loose={loose[k]})"
-    tight = ~loose
-    print(f"{prec}/{scheme}: max |err|/half-ulp on tight entries "
-          f"{(np.abs(got - ref)[tight] / _half_ulp(np.abs(ref[tight]) + delta, prec)).max():.3f}, "
-          f"loose entries {loose.mean():.2%}")
+    delta = 5e-8
+    h_prev, t_prev = s.state()
+    for _ in range(checks):
+        s.step(1)
+        h_next, _ = s.state()
+        o.set_state((_stored_to_f64(h_prev, prec) + w[:, None]).T, t_prev)
+        o.step(1)
+        ref = o.state().T - w[:, None]
+        got = _stored_to_f64(h_next, prec)
+        bound = _half_ulp(np.abs(ref) + delta, prec) + delta
+        site_max = np.abs(ref).max(axis=0)
+        mag = np.maximum(site_max[None, :], np.concatenate([site_max[None, :], site_max[y]]))
+        bound = np.where(loose, bound + 16 * _half_ulp(mag, prec), bound)
+        excess = np.abs(got - ref) - bound
+        k = np.unravel_index(excess.argmax(), excess.shape)
+        assert excess.max() <= 0.0, f"t={t_prev}: worst excess {excess.max():.3e} at {k} (loose={loose[k]})"
+        tight = ~loose
+        print(f"{prec}/{scheme} t={t_prev}: max |err|/half-ulp on tight entries "
+              f"{(np.abs(got - ref)[tight] / _half_ulp(np.abs(ref[tight]) + delta, prec)).max():.3f}, "
+              f"loose entries {loose.mean():.2%}")
+        h_prev, t_prev = h_next, t_prev + 1
     return o
 
 
+@pytest.mark.parametrize("wide", [False, True], ids=["off32", "off64"])
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_16bit_one_step_within_storage_rounding(d3q19, prec, scheme):
+def test_16bit_one_step_within_storage_rounding(d3q19, prec, scheme, wide):
     """Ragged several-tile tree (pulsatile inlet, 7 pressure outlets)."""
     _, w = d3q19
     lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0)
@@ -319,7 +325,7 @@ def test_16bit_one_step_within_storage_rounding(d3q19, prec, scheme):
         x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 200.0})
         for k in range(1, len(lat.iolets)):
             x.set_pressure(k, 1.0)
-    _one_step_within_rounding(lat, 0.55, bc, prec, scheme, w, warm=6 if scheme == "aa" else 5)
+    _one_step_within_rounding(lat, 0.55, bc, prec, scheme, w, wide=wide)
 
 
 def test_invalid_arguments(pipe):
