@@ -242,36 +242,48 @@ __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, 
 
 // After an AA step at time t: overwrite the slots that the iolet links of
 // each iolet site read in the next step with their boundary values, and
-// record the mass each link lets in.  One warp per iolet site, lane i =
-// direction i.  The site's stored post-collision populations s'_ibar(x) sit
-// in slot i of x after an even step, and in the slot it read direction i from
-// after an odd step; an iolet link's slot is slot i of x in both cases.
-// Boundary values use the moments of these stored values, as the A-B gather
-// does.
+// record the mass each link lets in.  One thread per iolet site: the whole
+// pass is one wave of threads, each with three rounds of independent loads
+// (index codes, stored populations, link records).  The site's stored
+// post-collision populations s'_ibar(x) sit in slot i of x after an even
+// step, and in the slot it read direction i from after an odd step; an iolet
+// link's slot is slot i of x in both cases.  Boundary values use the moments
+// of these stored values, as the A-B gather does.
 template <typename S, bool ODD>
-__global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict__ src,
+__global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict__ src,
                                                 const LinkRec* __restrict__ links, const double* __restrict__ amp,
                                                 const int32_t* __restrict__ sites, int64_t nsites,
                                                 const StepParams p, double* __restrict__ lflux) {
   using R = typename Real<S>::type;
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= nsites) return;  // uniform across the warp
-  const int i = threadIdx.x & 31;
-  const bool dir = i < Q;
-  const int64_t n = p.n, x = sites[w];
-  const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
-  R v = R(0);
-  if (dir) v = to_real(A[i == 0 ? x : (ODD ? aa_addr(i, code, n, x) : (int64_t)i * n + x)]);
-  // v = s'_ibar(x): rho = 1 + sum v, j = -sum v_i c_i
-  R d, jx, jy, jz;
-  lane_moment_sums<R>(v, R(-1), &d, &jx, &jy, &jz);
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nsites) return;
+  const int64_t n = p.n, x = sites[q];
+  int32_t code[Q];
+  code[0] = 0;
+#pragma unroll
+  for (int i = 1; i < Q; ++i) code[i] = src[(int64_t)(i - 1) * p.sn + x];
+  R v[Q];  // v[i] = s'_ibar(x), the value in the slot the link of direction i reads
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    v[i] = to_real(A[i == 0 ? x : (ODD ? aa_addr(i, code[i], n, x) : (int64_t)i * n + x)]);
+  R d = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {  // rho = 1 + sum v, j = -sum v_k c_k, in direction order
+    d += v[k];
+    if (cx(k)) jx += cx(k) > 0 ? -v[k] : v[k];
+    if (cy(k)) jy += cy(k) > 0 ? -v[k] : v[k];
+    if (cz(k)) jz += cz(k) > 0 ? -v[k] : v[k];
+  }
   const R rho = R(1) + d;
   const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
-  if (code <= -2) {
-    const LinkRec L = links[-code - 2];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const bool io = code[i] <= -2;
+    const LinkRec L = links[io ? -code[i] - 2 : 0];  // record 0 exists whenever a site has an iolet link
     const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
-    const R val = lane_iolet_value<R>(i, L, v, rho, ux, uy, uz, a, p);
-    lflux[-code - 2] = (double)val - (double)v;
+    if (!io) continue;
+    const R val = lane_iolet_value<R>(i, L, v[i], rho, ux, uy, uz, a, p);
+    lflux[-code[i] - 2] = (double)val - (double)v[i];
     A[(int64_t)i * n + x] = from_real<S>(val);
   }
 }
@@ -630,12 +642,12 @@ struct AAOp {
     else
       aa_even<S>(h, (S*)A, p, s);
     if (h->n_iolet_sites > 0) {
-      const unsigned g = (unsigned)((h->n_iolet_sites + 7) / 8);  // 8 warps (sites) per block
+      const unsigned g = (unsigned)((h->n_iolet_sites + 127) / 128);  // one thread per iolet site
       if (odd)
-        k_aa_fix<S, true><<<g, 256, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+        k_aa_fix<S, true><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
                                             h->n_iolet_sites, p, h->d_lflux);
       else
-        k_aa_fix<S, false><<<g, 256, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+        k_aa_fix<S, false><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
                                              h->n_iolet_sites, p, h->d_lflux);
     }
     return cudaGetLastError();
