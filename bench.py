@@ -62,7 +62,10 @@ ELEM = {"fp32": 4, "bf16": 2, "fp16": 2, "fp64": 8}
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": None, "bytes_per_site": {}}
+TRAFFIC = {"sha": "72ecef0861532b80",
+           # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site tree
+           "bytes_per_site": {"k_aa_odd32": (2960286208 + 1488272384) / 20000864,
+                              "k_step32": (3050513408 + 1482803968) / 20000864}}
 
 
 def kernel_sha() -> str:
@@ -447,6 +450,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": kst["gbs"], "peak": peak, "unit": "GB/s",
                          "frac": kst["gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": kname + "<float>", "launches": kst["launches"], "mean_us": kst["mean_us"],
+                         "timed": "CUDA events around each step" + (
+                             " (odd step = k_aa_odd32 + the k_aa_fix pass)" if scheme == "aa" else ""),
                          "algorithmic_bytes_per_site": kst["bytes_per_site"],
                          "step_gbs": head["gbs"], "step_bytes_per_site": head["bytes_per_site"]},
             "cpu_baseline": cpu,
