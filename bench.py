@@ -42,6 +42,11 @@ sys.path.insert(0, str(ROOT))
 METRIC = "fluid-site MLUPS and HBM GB/s (% of peak), FP32 vs 16-bit store; adjoint/fwd"
 WORKLOAD = "seeded depth-6 vessel tree, 20M fluid sites, D3Q19 LBGK tau=0.55, pulsatile Ladd inlet, 64 pressure outlets"
 
+
+def workload_name(n, tau):
+    return (f"seeded depth-6 vessel tree, {n / 1e6:.0f}M fluid sites, D3Q19 LBGK tau={tau:g}, "
+            "pulsatile Ladd inlet, 64 pressure outlets")
+
 # Algorithmic bytes per site update (storage element size e): 19 populations
 # read + 19 written, plus the int32 streaming-index table (18 x 4 B) when the
 # kernel gathers through it.  Pull A-B gathers every step; the AA pattern
@@ -442,10 +447,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 storage, f32 math", "fp16": "f16 storage, f32 math", "fp64": "f64"}[prec0], "data": "synthetic",
-            "config": {"workload": WORKLOAD if n < 100_000_000 else WORKLOAD.replace("20M", f"{n / 1e6:.0f}M"),
-                       "n_sites": n, "tau": args.tau,
+            "config": {"workload": workload_name(n, args.tau), "n_sites": n, "tau": args.tau,
                        "scheme": {"ab": "pull A-B", "aa": "AA pattern"}[scheme],
-                       "parallelism": f"replicas x{world}", "l2": "working set 4.5 GB/step >> 129 MB L2, no flush",
+                       "parallelism": f"replicas x{world}", "l2": f"working set {n * head['bytes_per_site'] / 1e9:.1f} GB/step >> 129 MB L2, no flush",
                        "fill": round(lat.info["fill"], 4)},
             "roofline": {"bound": "hbm", "achieved": kst["gbs"], "peak": peak, "unit": "GB/s",
                          "frac": kst["gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,

@@ -207,6 +207,17 @@ int hlb_read_macros(hlb_solver* h, float* rho, float* u, float* wss, int32_t whe
  * HLB_ERR_DIVERGED if the mass is not finite. */
 int hlb_reduce(hlb_solver* h, double* mass, double* iolet_flux);
 
+/* Iolet monitor of the current state f(t), the quantities of the paper's
+ * pipe validation (Section 6: volumetric flow rate, maximum velocity and
+ * pressure at the inlet and the outlet), per iolet k, each array
+ * [n_iolets] on the host, any of them NULL:
+ *   flux[k]     mass that entered through iolet k in the step that produced
+ *               f(t), as hlb_reduce reports it (flow rate x density);
+ *   u_max[k]    max |u| over the sites with a link to iolet k;
+ *   rho_mean[k] mean density over those sites (pressure = rho_mean / 3).
+ * FP64, deterministic; synchronises the solver's stream. */
+int hlb_iolet_monitor(hlb_solver* h, double* flux, double* u_max, double* rho_mean);
+
 /* Shifted pre-collision state h_i = f_i(t) - w_i as [19][N] in the storage
  * precision (host or device per `where`), and its time t.  set_state
  * resumes from such a state. */

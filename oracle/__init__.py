@@ -60,6 +60,8 @@ def _load():
         lib.ora_mass.argtypes = [_P]
         lib.ora_mass.restype = C.c_double
         lib.ora_flux.argtypes = [_P, _D]
+        lib.ora_wave_value.argtypes = [_P, C.c_int, C.c_double]
+        lib.ora_wave_value.restype = C.c_double
         lib.ora_macros.argtypes = [_P, _D, _D, _D, C.POINTER(C.c_float)]
         lib.ora_objective.argtypes = [_P, C.c_int64, C.c_int64, _I64, _D, _D]
         lib.ora_objective.restype = C.c_double
@@ -200,6 +202,11 @@ class Oracle:
         out = np.zeros(max(self.nio, 1), np.float64)
         self._lib.ora_flux(self._h, _ptr(out, C.c_double))
         return out[: self.nio]
+
+    def wave_value(self, k: int, t: float) -> float:
+        """Waveform of iolet k at time t (velocity: the w(t) multiplying the
+        amplitudes; pressure: the ghost density)."""
+        return float(self._lib.ora_wave_value(self._h, int(k), float(t)))
 
     # ---- objective / adjoint ----
     def objective(self, nsteps, sites, target, axis) -> float:

@@ -271,6 +271,11 @@ int ora_set_velocity(ora_t* o, int k, const double* amps, int ngroups, int kind,
   for (int g = 0; g < ngroups; ++g) o->amp[o->io[k].goff + g] = amps[g];
   return set_wave(&o->io[k].wave, kind, mean, rel, period, phase, nsamp, samp);
 }
+/* Value of iolet k's waveform at time t (test access to wave_at). */
+double ora_wave_value(const ora_t* o, int k, double t) {
+  if (k < 0 || k >= o->nio) return NAN;
+  return wave_at(&o->io[k].wave, t);
+}
 /* Pressure iolet k: ghost density rho(t) = w(t). */
 int ora_set_pressure(ora_t* o, int k, int kind, double mean, double rel, double period,
                      double phase, int nsamp, const double* samp) {

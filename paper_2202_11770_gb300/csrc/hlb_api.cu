@@ -116,8 +116,8 @@ StepParams hlb_solver::params(int64_t tb) const {
 namespace {
 
 struct Layout {
-  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, err = 0,
-         total = 0;
+  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, ioff = 0,
+         ilist = 0, mon = 0, err = 0, total = 0;
   int64_t n_links = 0;
   int32_t n_groups = 0;
 };
@@ -195,6 +195,9 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.red = off; off += align_up(sizeof(double) * (size_t)hlb_reduce_slots(n, L->n_iolets));
   y.lflux = off; off += align_up(sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.isites = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(n_iolet_sites, 1));
+  y.ioff = off; off += align_up(sizeof(int64_t) * (size_t)(L->n_iolets + 1));
+  y.ilist = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(y.n_links, 1));  // >= sites per iolet
+  y.mon = off; off += align_up(sizeof(double) * 2 * (size_t)std::max(L->n_iolets, 1));
   y.err = off; off += 256;
   y.total = off;
   return y;
@@ -274,6 +277,9 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->d_lflux = (double*)(base + y.lflux);
   h->d_err = (int*)(base + y.err);
   h->d_iolet_sites = (int32_t*)(base + y.isites);
+  h->d_ioff = (int64_t*)(base + y.ioff);
+  h->d_ilist = (int32_t*)(base + y.ilist);
+  h->d_mon = (double*)(base + y.mon);
   h->n_iolet_sites = nis;
 
   // link records sorted by (iolet, group, site, direction)
@@ -364,6 +370,28 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
     e = cudaMemcpyAsync(h->d_red + nb, begin.data(), sizeof(int64_t) * begin.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nis > 0)
     e = cudaMemcpyAsync(h->d_iolet_sites, isites.data(), sizeof(int32_t) * (size_t)nis, cudaMemcpyHostToDevice, st);
+  // sites of each iolet (a link to it), ascending, as ranges of one list
+  std::vector<std::vector<int32_t>> per_io((size_t)h->n_iolets);
+  for (int32_t x : isites) {
+    for (int i = 1; i < Q; ++i) {
+      const int32_t c = L->src[(int64_t)(i - 1) * n + x];
+      if (c > -2) continue;
+      const int k = -c - 2;
+      bool seen = false;
+      for (int j = 1; j < i && !seen; ++j) seen = L->src[(int64_t)(j - 1) * n + x] == c;
+      if (!seen) per_io[(size_t)k].push_back(x);
+    }
+  }
+  std::vector<int64_t> ioff((size_t)h->n_iolets + 1, 0);
+  std::vector<int32_t> ilist;
+  for (int k = 0; k < h->n_iolets; ++k) {
+    ilist.insert(ilist.end(), per_io[(size_t)k].begin(), per_io[(size_t)k].end());
+    ioff[(size_t)k + 1] = (int64_t)ilist.size();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_ioff, ioff.data(), sizeof(int64_t) * ioff.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !ilist.empty())
+    e = cudaMemcpyAsync(h->d_ilist, ilist.data(), sizeof(int32_t) * ilist.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_lflux, 0, sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->state_bytes(), st);  // rest: h = f - w = 0
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -505,6 +533,30 @@ extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
   if (flux)
     for (int k = 0; k < h->n_iolets; ++k) flux[k] = host[1 + k];
   if (!std::isfinite(host[0])) return hlb_fail(HLB_ERR_DIVERGED, "mass is not finite");
+  return HLB_OK;
+}
+
+extern "C" int hlb_iolet_monitor(hlb_solver* h, double* flux, double* u_max, double* rho_mean) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  const int K = h->n_iolets;
+  if (K == 0) return HLB_OK;
+  if (flux) {
+    std::vector<double> fl((size_t)K);
+    int rc = hlb_reduce(h, nullptr, fl.data());
+    if (rc) return rc;
+    for (int k = 0; k < K; ++k) flux[k] = fl[(size_t)k];
+  }
+  if (!u_max && !rho_mean) return HLB_OK;
+  CUDA_TRY(hlb_launch_monitor(h, h->f[h->cur], h->phase, h->t - 1, h->d_mon, h->stream));
+  std::vector<double> host(2 * (size_t)K);
+  CUDA_TRY(cudaMemcpyAsync(host.data(), h->d_mon, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  int rc = hlb_check_device_error(h);
+  if (rc) return rc;
+  for (int k = 0; k < K; ++k) {
+    if (u_max) u_max[k] = host[(size_t)k];
+    if (rho_mean) rho_mean[k] = host[(size_t)(K + k)];
+  }
   return HLB_OK;
 }
 

@@ -673,6 +673,57 @@ struct MacroOp {
   }
 };
 
+// Per-iolet monitor of f(t): block k walks the sites with a link to iolet k
+// (ilist[ioff[k] .. ioff[k+1])) and writes out[k] = max |u| and
+// out[K + k] = mean rho over them.  Per-thread partial sums run in a fixed
+// stride order and the block combines them in a fixed tree, so the result
+// does not depend on scheduling.
+template <typename S, int MODE>
+__global__ void __launch_bounds__(256) k_iolet_monitor(const S* __restrict__ fin, const int32_t* __restrict__ src,
+                                                       const LinkRec* __restrict__ links,
+                                                       const double* __restrict__ amp, const StepParams p,
+                                                       const int64_t* __restrict__ ioff,
+                                                       const int32_t* __restrict__ ilist, double* __restrict__ out) {
+  using R = typename Real<S>::type;
+  __shared__ double smax[256], ssum[256];
+  const int k = blockIdx.x;
+  const int64_t b = ioff[k], e = ioff[k + 1];
+  double umax = 0.0, rsum = 0.0;
+  for (int64_t q = b + threadIdx.x; q < e; q += blockDim.x) {
+    R h[Q];
+    load_state<S, MODE>(fin, src, links, amp, p, ilist[q], h);
+    const Macro<R> m = moments<R>(h);
+    const double u2 = (double)m.ux * m.ux + (double)m.uy * m.uy + (double)m.uz * m.uz;
+    umax = fmax(umax, sqrt(u2));
+    rsum += (double)m.rho;
+  }
+  smax[threadIdx.x] = umax;
+  ssum[threadIdx.x] = rsum;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+      ssum[threadIdx.x] += ssum[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[k] = smax[0];
+    out[gridDim.x + k] = e > b ? ssum[0] / (double)(e - b) : 0.0;
+  }
+}
+
+template <typename S>
+struct MonitorOp {
+  static cudaError_t run(const hlb_solver* h, const void* fin, int mode, int64_t tb, double* out, cudaStream_t s) {
+    if (h->n_iolets == 0) return cudaSuccess;
+    StepParams p = h->params(tb);
+    HLB_MODE_SWITCH(mode, (k_iolet_monitor<S, M><<<h->n_iolets, 256, 0, s>>>(
+                              (const S*)fin, h->d_src, h->d_links, h->d_amp, p, h->d_ioff, h->d_ilist, out)));
+    return cudaGetLastError();
+  }
+};
+
 template <typename S>
 struct StateOp {
   static cudaError_t run(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
@@ -734,6 +785,10 @@ cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cud
 cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, int mode, int64_t tb, float* rho, float* u,
                               float* wss, cudaStream_t s) {
   return dispatch<MacroOp>(h->precision, h, fin, mode, tb, rho, u, wss, s);
+}
+cudaError_t hlb_launch_monitor(const hlb_solver* h, const void* fin, int mode, int64_t tb, double* out,
+                               cudaStream_t s) {
+  return dispatch<MonitorOp>(h->precision, h, fin, mode, tb, out, s);
 }
 cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
                              cudaStream_t s) {

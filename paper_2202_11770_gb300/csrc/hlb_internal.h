@@ -63,6 +63,9 @@ struct hlb_solver {
   int* d_err = nullptr;               // set by device code when a bounded wait runs out
   double* d_lflux = nullptr;          // [n_links] mass let in by each iolet link in the last AA step
   int32_t* d_iolet_sites = nullptr;   // sites with at least one iolet link (AA boundary fix-up)
+  int64_t* d_ioff = nullptr;          // [n_iolets + 1] ranges of d_ilist per iolet
+  int32_t* d_ilist = nullptr;         // sites with a link to iolet k, ascending, iolet by iolet
+  double* d_mon = nullptr;            // [2][n_iolets] monitor outputs
   int64_t n_iolet_sites = 0;
   int64_t red_slots = 0;
 
@@ -87,6 +90,9 @@ cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cud
 // rho, u [3][n], wss of the current state, device outputs (any may be null).
 cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, int mode, int64_t tb, float* rho, float* u,
                               float* wss, cudaStream_t s);
+// Per-iolet max |u| (out[k]) and mean rho (out[K + k]) over the sites linked to iolet k.
+cudaError_t hlb_launch_monitor(const hlb_solver* h, const void* fin, int mode, int64_t tb, double* out,
+                               cudaStream_t s);
 // Shifted pre-collision state into out [19][n] (row < 0) or direction `row` into out [n].
 cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
                              cudaStream_t s);

@@ -84,6 +84,7 @@ _PROTOS = {
     "hlb_time": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "hlb_read_macros": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
     "hlb_reduce": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "hlb_iolet_monitor": (C.c_int, [_P, _P, _P, _P]),
     "hlb_get_state": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int64)]),
     "hlb_set_state": (C.c_int, [_P, _P, C.c_int32, C.c_int64]),
     "hlb_adjoint_workspace_bytes": (C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]),
@@ -332,6 +333,14 @@ class Solver:
         if rc == HLB_ERR_DIVERGED:
             raise HlbError(rc, library().hlb_last_error().decode())
         return mass, flux
+
+    def iolet_monitor(self):
+        """Per iolet: (mass flux of the last step, max |u|, mean rho) over the
+        sites linked to it, FP64 arrays [n_iolets] (pressure = rho / 3)."""
+        k = len(self.iolets)
+        flux, umax, rho = (np.zeros(k), np.zeros(k), np.zeros(k))
+        _check(self._lib.hlb_iolet_monitor(self._h, _P(flux.ctypes.data), _P(umax.ctypes.data), _P(rho.ctypes.data)))
+        return flux, umax, rho
 
     def state(self):
         """Host copy of the shifted pre-collision state [19, n] (storage dtype) and t."""
