@@ -7,8 +7,8 @@ with a parabolic cross-section weight, rho = 1 at every outlet.  Inputs are
 synthetic and seeded; the paper's patient geometries are not available.
 
 One benchmark step = one LB time step over the whole lattice: one launch of
-the fused stream-collide-boundary kernel (pull A-B: k_step32, iolet sites
-included), or for the AA pattern k_aa_odd32 / k_aa_even (alternating) plus
+the fused stream-collide-boundary kernel (pull A-B: k_step, iolet sites
+included), or for the AA pattern k_aa_odd / k_aa_even (alternating) plus
 the k_aa_fix pass over the iolet sites (0.2 % of the sites).  ``value`` is MLUPS (Eq. 9 of arXiv
 2202.11770) with the lattice resident in HBM; the state (~4.5 GB touched per
 step) is far larger than L2, so no flush is needed between steps.
@@ -69,8 +69,8 @@ ELEM = {"fp32": 4, "bf16": 2, "fp16": 2, "fp64": 8}
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
 TRAFFIC = {"sha": "72ecef0861532b80",
            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site tree
-           "bytes_per_site": {"k_aa_odd32": (2960286208 + 1488272384) / 20000864,
-                              "k_step32": (3050513408 + 1482803968) / 20000864}}
+           "bytes_per_site": {"k_aa_odd": (2960286208 + 1488272384) / 20000864,
+                              "k_step": (3050513408 + 1482803968) / 20000864}}
 
 
 def kernel_sha() -> str:
@@ -193,10 +193,8 @@ def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55)
 
 
 def kernel_names(n):
-    """Names of the step kernels the library launches for n sites: the
-    32-bit-offset kernels while 19 x the index row stride fits in 32 bits."""
-    off32 = 19 * (-(-n // 4) * 4) <= 0xFFFFFFFF
-    return ("k_step32", "k_aa_odd32") if off32 else ("k_step", "k_aa_odd")
+    """Names of the step kernels the library launches (pull A-B, AA odd step)."""
+    return ("k_step", "k_aa_odd")
 
 
 def form_stats(lat, precision, scheme, total, durs, t_first, steps, peak):
@@ -455,7 +453,7 @@ def run_ours(args):
                          "frac": kst["gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": kname + "<float>", "launches": kst["launches"], "mean_us": kst["mean_us"],
                          "timed": "CUDA events around each step" + (
-                             " (odd step = k_aa_odd32 + the k_aa_fix pass)" if scheme == "aa" else ""),
+                             " (odd step = k_aa_odd + the k_aa_fix pass)" if scheme == "aa" else ""),
                          "algorithmic_bytes_per_site": kst["bytes_per_site"],
                          "step_gbs": head["gbs"], "step_bytes_per_site": head["bytes_per_site"]},
             "cpu_baseline": cpu,

@@ -112,12 +112,13 @@ typedef struct {
  * ladd_rho_one: 1 = use rho = 1 in the Ladd correction instead of the
  *   site's density (the paper does not say which density).
  * ghost_full_u: 1 = pressure-iolet ghost velocity u instead of (u.n) n.
- * wide_offsets: 1 = always address populations and the index table with
- *   64-bit element offsets.  The step and adjoint kernels use 32-bit offsets
- *   whenever 19 x the index row stride fits in 32 bits (up to about 226M
- *   sites) and 64-bit ones above; this flag selects the 64-bit kernels at
- *   any size, so that they can be checked on small lattices.  Results are
- *   identical either way. */
+ * wide_offsets: 1 = always use the large-lattice addressing of the step
+ *   and adjoint kernels.  They keep per-site offsets in 32 bits: measured
+ *   from the array base while 19 x the index row stride fits (up to about
+ *   226M sites), and from the start of the direction pair (rows 2p-1, 2p)
+ *   above that, which covers any lattice below 2^31 sites.  This flag selects
+ *   the second form at any size, so that it can be checked on small
+ *   lattices.  Results are identical either way. */
 typedef struct {
   int32_t precision;
   int32_t scheme;

@@ -88,13 +88,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // plus the probe term.  The index row is read twice (once per gather); the
 // second read hits L1.  A TMA-staged index tile (as in k_step) measured no
 // faster here and costs 56 KiB of shared memory per block.
-template <typename S, bool GPREV, typename I>
+template <typename S, bool GPREV, bool WIDE>
 __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const S* __restrict__ mu_next,
                                                S* __restrict__ mu_out, const int32_t* __restrict__ src,
                                                const AdjParams& ap, const ProbeMap& pm, int store, int64_t x,
                                                typename Real<S>::type (*neq)[BLOCK]) {
   using R = typename Real<S>::type;
-  const I n = (I)ap.prev.n, sn = (I)ap.prev.sn, xi = (I)x;
+  const uint32_t n = (uint32_t)ap.prev.n, sn = (uint32_t)ap.prev.sn, xi = (uint32_t)x;
   const R omega = R(ap.prev.omega);
   double dtau_local = 0;
   bool iolet = x >= ap.prev.n;
@@ -104,8 +104,10 @@ __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const
     h[0] = ldpop(prev + xi);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int32_t s = __ldg(src + (I)(i - 1) * sn + xi);
-      h[i] = ldpop(prev + (GPREV ? (s >= 0 ? (I)i * n + (I)s : (I)opp(i) * n + xi) : (I)i * n + xi));
+      const int32_t s = __ldg(idx_at<WIDE>(src, i, sn, xi));
+      h[i] = ldpop(at<WIDE>(prev, i, n,
+                            GPREV ? (s >= 0 ? slot<WIDE>(i, n, (uint32_t)s) : slot<WIDE>(opp(i), n, xi))
+                                  : slot<WIDE>(i, n, xi)));
       iolet |= s <= -2;
     }
     if (!iolet) {  // iolet sites: k_adjoint_iolet
@@ -120,9 +122,9 @@ __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const
     lam[0] = ldpop(mu_next + xi);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const int32_t s = __ldca(src + (I)(i - 1) * sn + xi);  // a re-read, not held in registers
+      const int32_t s = __ldca(idx_at<WIDE>(src, i, sn, xi));  // a re-read, not held in registers
       // s'_opp(i)(x) is read by x - c_i = x + c_opp(i) in direction opp(i)
-      lam[opp(i)] = ldpop(mu_next + (s >= 0 ? (I)opp(i) * n + (I)s : (I)i * n + xi));
+      lam[opp(i)] = ldpop(at<WIDE>(mu_next, i, n, s >= 0 ? slot<WIDE>(opp(i), n, (uint32_t)s) : slot<WIDE>(i, n, xi)));
     }
     const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     R S0 = R(0), Lw = R(0), Bx = R(0), By = R(0), Bz = R(0), dt = R(0);
@@ -155,7 +157,7 @@ __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const
         if (cx(j)) v += cx(j) > 0 ? Ex : -Ex;
         if (cy(j)) v += cy(j) > 0 ? Ey : -Ey;
         if (cz(j)) v += cz(j) > 0 ? Ez : -Ez;
-        mu_out[(I)j * n + xi] = from_real<S>(v);
+        *(j == 0 ? mu_out + xi : at<WIDE>(mu_out, j, n, slot<WIDE>(j, n, xi))) = from_real<S>(v);
       }
     }
   }
@@ -323,9 +325,10 @@ __device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev,
 // take 256 bulk sites, a thread each.  Spreading the short, latency-bound
 // iolet blocks through the grid lets them run beside the bulk blocks instead
 // of ahead of them.  Block b's dJ/dtau partial goes to part[b] (fixed order).
-// I is the element-offset type: 32-bit whenever 19 x the row stride fits,
-// which keeps the 38 gather addresses from spilling.
-template <typename S, bool GPREV, typename I>
+// WIDE: offsets within direction pairs (lattices above ~226M sites); the
+// offsets stay 32-bit either way, which keeps the 38 gather addresses from
+// spilling.
+template <typename S, bool GPREV, bool WIDE>
 __global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2 : 4)
     k_adjoint(const S* __restrict__ prev, const S* __restrict__ cur, const S* __restrict__ mu_next,
               S* __restrict__ mu_out, const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2
                                      store, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
   } else {
     const unsigned k = b - min(n_iolet_blocks, j + 1);  // bulk tile: blocks before b that are not iolet blocks
-    d = adjoint_site<S, GPREV, I>(prev, mu_next, mu_out, src, ap, pm, store, (int64_t)k * BLOCK + threadIdx.x, neq);
+    d = adjoint_site<S, GPREV, WIDE>(prev, mu_next, mu_out, src, ap, pm, store, (int64_t)k * BLOCK + threadIdx.x, neq);
   }
   const double bs = block_sum(d, sh);
   if (threadIdx.x == 0) part[b] += bs;
@@ -409,8 +412,8 @@ cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, co
   const unsigned grid = gi + grid_for(h->n);
   const unsigned stride = gi ? grid / gi : 1;  // gi * stride <= grid
   const bool off32 = h->off32;
-  auto kernel = gprev ? (off32 ? k_adjoint<S, true, uint32_t> : k_adjoint<S, true, int64_t>)
-                      : (off32 ? k_adjoint<S, false, uint32_t> : k_adjoint<S, false, int64_t>);
+  auto kernel = gprev ? (off32 ? k_adjoint<S, true, false> : k_adjoint<S, true, true>)
+                      : (off32 ? k_adjoint<S, false, false> : k_adjoint<S, false, true>);
   kernel<<<grid, BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src, h->d_links,
                                  h->d_amp, ap, pm, h->d_iolet_sites, h->n_iolet_sites, gi, stride, dtau_part, dlink,
                                  st_);
@@ -592,7 +595,6 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   TRY(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
 #undef TRY
-  if (int rc = hlb_check_device_error(h)) return rc;
   h->cur = 0;
   h->phase = fin_mode;
   h->stepped = h->scheme == HLB_AA;

@@ -34,13 +34,6 @@ int hlb_cuda_fail(cudaError_t e, const char* where) {
 
 extern "C" const char* hlb_last_error(void) { return g_err.c_str(); }
 
-int hlb_check_device_error(hlb_solver* h) {
-  int flag = 0;
-  CUDA_TRY(cudaMemcpyAsync(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(cudaStreamSynchronize(h->stream));
-  if (flag) return hlb_fail(HLB_ERR_CUDA, "a device wait for a staged index tile timed out; results are invalid");
-  return HLB_OK;
-}
 extern "C" int hlb_version(void) { return 10100; }
 
 // ---------------------------------------------------------------------------
@@ -117,7 +110,7 @@ namespace {
 
 struct Layout {
   size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, ioff = 0,
-         ilist = 0, mon = 0, err = 0, total = 0;
+         ilist = 0, mon = 0, total = 0;
   int64_t n_links = 0;
   int32_t n_groups = 0;
 };
@@ -198,7 +191,6 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.ioff = off; off += align_up(sizeof(int64_t) * (size_t)(L->n_iolets + 1));
   y.ilist = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(y.n_links, 1));  // >= sites per iolet
   y.mon = off; off += align_up(sizeof(double) * 2 * (size_t)std::max(L->n_iolets, 1));
-  y.err = off; off += 256;
   y.total = off;
   return y;
 }
@@ -275,7 +267,6 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->d_red = (double*)(base + y.red);
   h->red_slots = hlb_reduce_slots(n, h->n_iolets);
   h->d_lflux = (double*)(base + y.lflux);
-  h->d_err = (int*)(base + y.err);
   h->d_iolet_sites = (int32_t*)(base + y.isites);
   h->d_ioff = (int64_t*)(base + y.ioff);
   h->d_ilist = (int32_t*)(base + y.ilist);
@@ -360,7 +351,6 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
       }
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
   if (e == cudaSuccess && y.n_links > 0)
     e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(double) * ampf.size(), cudaMemcpyHostToDevice, st);
@@ -516,7 +506,7 @@ extern "C" int hlb_read_macros(hlb_solver* h, float* rho, float* u, float* wss, 
   if (u) CUDA_TRY(cudaMemcpyAsync(u, su, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, h->stream));
   if (wss) CUDA_TRY(cudaMemcpyAsync(wss, sw, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  return hlb_check_device_error(h);
+  return HLB_OK;
 }
 
 extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
@@ -527,8 +517,6 @@ extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
   std::vector<double> host(1 + h->n_iolets);
   CUDA_TRY(cudaMemcpyAsync(host.data(), out, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  int rc = hlb_check_device_error(h);
-  if (rc) return rc;
   if (mass) *mass = host[0];
   if (flux)
     for (int k = 0; k < h->n_iolets; ++k) flux[k] = host[1 + k];
@@ -551,8 +539,6 @@ extern "C" int hlb_iolet_monitor(hlb_solver* h, double* flux, double* u_max, dou
   std::vector<double> host(2 * (size_t)K);
   CUDA_TRY(cudaMemcpyAsync(host.data(), h->d_mon, sizeof(double) * host.size(), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
-  int rc = hlb_check_device_error(h);
-  if (rc) return rc;
   for (int k = 0; k < K; ++k) {
     if (u_max) u_max[k] = host[(size_t)k];
     if (rho_mean) rho_mean[k] = host[(size_t)(K + k)];
@@ -582,7 +568,7 @@ extern "C" int hlb_get_state(hlb_solver* h, void* f, int32_t where, int64_t* t) 
     }
   }
   if (t) *t = h->t;
-  if (where == HLB_HOST) return hlb_check_device_error(h);
+  if (where == HLB_HOST) CUDA_TRY(cudaStreamSynchronize(h->stream));
   return HLB_OK;
 }
 

@@ -358,98 +358,30 @@ __device__ __forceinline__ void load_state(const S* __restrict__ fin, const int3
 }
 
 // ---------------------------------------------------------------------------
-// Index tiles staged in shared memory by the Tensor Memory Accelerator.
-//
-// Persistent kernels walk tiles of TILE consecutive sites; one thread per CTA
-// copies the next tile's 18 index rows (18 x TILE int32, contiguous in each
-// row) into the other half of a double buffer with cp.async.bulk, completing
-// on an mbarrier, while the CTA works on the current tile.  Index rows have
-// a stride that is a multiple of 4 sites and tiles start at multiples of
-// TILE, so every copy starts on a 16-byte boundary and moves a multiple of
-// 16 bytes.  Waits are bounded: a wait that runs out records an error in
-// *err and the tile is skipped (no index from an unfinished copy is used).
+// Offsets of the hot kernels.  A thread keeps up to 18 slot offsets in
+// registers, so they are 32-bit.  With WIDE = false (19 x the index row
+// stride below 2^32, about 226M sites) an offset is the element offset from
+// the array base.  With WIDE = true it is the offset within the direction
+// pair (2p-1, 2p), p = (i + 1) / 2, whose two rows are contiguous and start
+// at element (2p - 1) n: every gather or store of a step touches only
+// direction i and opp(i), both in that pair, and offsets there stay below
+// 2n < 2^32 for any lattice of fewer than 2^31 sites.  The 64-bit pair start
+// is added when the address is formed.
 // ---------------------------------------------------------------------------
-constexpr int TILE = 256;
-constexpr int WAIT_LIMIT = 1 << 22;
-
-// 128-byte aligned: bulk-copy destinations must start on 16-byte boundaries
-// (each row is TILE * 4 = 1 KiB, so every row start stays aligned).
-struct __align__(128) IdxTiles {
-  int32_t idx[2][Q - 1][TILE];
-  unsigned long long bar[2];
-};
-static_assert(sizeof(int32_t) * TILE % 16 == 0, "index rows must keep 16-byte alignment");
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void tile_init(IdxTiles& t) {
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&t.bar[0])) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&t.bar[1])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
+// offset of row `row` (i or opp(i), i >= 1) at site e
+template <bool WIDE>
+__device__ __forceinline__ uint32_t slot(int row, uint32_t n, uint32_t e) {
+  return WIDE ? ((row & 1) ? e : n + e) : (uint32_t)row * n + e;
 }
-
-// One thread: stage the index rows of `tile` into buffer b.
-__device__ __forceinline__ void tile_issue(IdxTiles& t, int b, const int32_t* __restrict__ src, int64_t n,
-                                           int64_t sn, int64_t tile) {
-  const int64_t start = tile * TILE;
-  const int64_t left = n - start;
-  const uint32_t cnt = (uint32_t)(left < TILE ? ((left + 3) & ~(int64_t)3) : TILE);
-  const uint32_t bytes = cnt * 4u;
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
-               ::"r"(smem_addr(&t.bar[b])), "r"(bytes * (Q - 1)) : "memory");
-#pragma unroll 1
-  for (int i = 0; i < Q - 1; ++i)
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_addr(&t.idx[b][i][0])), "l"(src + (int64_t)i * sn + start), "r"(bytes),
-                 "r"(smem_addr(&t.bar[b]))
-                 : "memory");
+// address of a slot of direction i's pair
+template <bool WIDE, typename T>
+__device__ __forceinline__ T* at(T* a, int i, uint32_t n, uint32_t off) {
+  return WIDE ? a + ((uint64_t)(2 * ((i + 1) >> 1) - 1) * n + off) : a + off;
 }
-
-// All threads: wait (bounded) for buffer b's copy of the given phase parity.
-__device__ __forceinline__ bool tile_wait(IdxTiles& t, int b, uint32_t parity, int* err) {
-  for (int it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t done;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done) : "r"(smem_addr(&t.bar[b])), "r"(parity) : "memory");
-    if (done) return true;
-  }
-  atomicExch(err, 1);
-  return false;
-}
-
-// Persistent tile loop shared by the gather kernels: for every tile owned by
-// this CTA, stage its index rows (prefetching the next tile's), then call
-// body(x, codes_row0, ok).  `ok` is false only when the index copy did not
-// complete in time (the error word is set and the tile is skipped).
-template <typename Body>
-__device__ __forceinline__ void tile_loop(IdxTiles& t, const int32_t* __restrict__ src, int64_t n, int64_t sn,
-                                          int* err, Body body) {
-  const int64_t ntiles = (n + TILE - 1) / TILE;
-  tile_init(t);
-  int64_t tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) tile_issue(t, 0, src, n, sn, tile);
-  int b = 0;
-  uint32_t par0 = 0u, par1 = 0u;  // phase parity expected next on each buffer's barrier
-  bool missed = false;
-  for (; tile < ntiles; tile += gridDim.x) {
-    const int64_t next = tile + gridDim.x;
-    if (threadIdx.x == 0 && next < ntiles) tile_issue(t, b ^ 1, src, n, sn, next);
-    const bool ok = tile_wait(t, b, b ? par1 : par0, err);
-    missed |= !ok;
-    if (b) par1 ^= 1u; else par0 ^= 1u;
-    body(tile * TILE + threadIdx.x, &t.idx[b][0][threadIdx.x], ok);
-    __syncthreads();  // every thread is done with buffer b before it is refilled
-    b ^= 1;
-  }
-  // a copy that timed out may still be in flight: wait for it (bounded) before leaving
-  if (missed && threadIdx.x == 0) {
-    tile_wait(t, 0, par0 ^ 1u, err);
-    tile_wait(t, 1, par1 ^ 1u, err);
-  }
+// index code of direction i >= 1 at site x (rows of stride sn)
+template <bool WIDE>
+__device__ __forceinline__ const int32_t* idx_at(const int32_t* src, int i, uint32_t sn, uint32_t x) {
+  return WIDE ? src + ((uint64_t)(i - 1) * sn + x) : src + (uint32_t)(i - 1) * sn + x;
 }
 
 }  // namespace hlb

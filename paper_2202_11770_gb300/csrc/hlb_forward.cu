@@ -8,7 +8,7 @@
 // per-site fix-up.  Two streaming schemes:
 //
 //  * pull A-B (k_step): read buffer A by gathering through the index table,
-//    write buffer B in place; 224 B per FP32 site update.
+//    write buffer B; 224 B per FP32 site update.
 //  * AA pattern (k_aa_even / k_aa_odd, then k_aa_fix over iolet sites): one
 //    buffer.  Even steps read a site's 19 slots and write them back swapped
 //    (no index table); odd steps read 19 slots through the index table and
@@ -52,32 +52,6 @@ __global__ void __launch_bounds__(BLOCK) k_step_local(const S* __restrict__ fin,
   for (int i = 0; i < Q; ++i) stpop<S>(fout + (int64_t)i * n + x, h[i]);
 }
 
-// Pull A-B step from s'(t-1): gather f(t) through the staged index tile,
-// collide, store.  Sites with iolet links are written by k_step_iolet.
-template <typename S>
-__global__ void __launch_bounds__(TILE, 5) k_step(const S* __restrict__ fin, S* __restrict__ fout,
-                                               const int32_t* __restrict__ src, const StepParams p, int* err) {
-  using R = typename Real<S>::type;
-  __shared__ IdxTiles t;
-  const int64_t n = p.n;
-  tile_loop(t, src, n, p.sn, err, [&](int64_t x, const int32_t* codes, bool ok) {
-    if (!ok || x >= n) return;
-    R h[Q];
-    h[0] = ldpop(fin + x);
-    bool iolet = false;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int32_t s = codes[(i - 1) * TILE];
-      h[i] = ldpop(fin + (s >= 0 ? (int64_t)i * n + s : (int64_t)opp(i) * n + x));
-      iolet |= s <= -2;
-    }
-    collide<R>(h, R(p.omega));
-    if (iolet) return;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) stpop<S>(fout + (int64_t)i * n + x, h[i]);
-  });
-}
-
 // The same step for the sites with iolet links: one warp per site, lane i
 // handles direction i (gather, boundary value, collision), with the moment
 // sums in direction order so that every value equals the per-thread
@@ -115,30 +89,19 @@ __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __
   }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(256) k_step_iolet(const S* __restrict__ fin, S* __restrict__ fout,
-                                                    const int32_t* __restrict__ src,
-                                                    const LinkRec* __restrict__ links,
-                                                    const double* __restrict__ amp,
-                                                    const int32_t* __restrict__ sites, int64_t nsites,
-                                                    const StepParams p) {
-  step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p,
-                     ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-}
-
-// Pull A-B step in one launch with 32-bit element offsets (19 x the row
-// stride fits in 32 bits) and no staged index tiles.  Every stride-th block
-// (the first n_iolet_blocks of them) takes eight iolet sites, a warp each,
-// exactly as k_step_iolet; the others take 256 bulk sites, a thread each.
-// The iolet blocks, spread through the grid, run beside the bulk blocks
-// instead of after them.
-template <typename S>
-__global__ void __launch_bounds__(BLOCK, 5) k_step32(const S* __restrict__ fin, S* __restrict__ fout,
-                                                  const int32_t* __restrict__ src,
-                                                  const LinkRec* __restrict__ links,
-                                                  const double* __restrict__ amp,
-                                                  const int32_t* __restrict__ sites, int64_t nsites,
-                                                  unsigned n_iolet_blocks, unsigned stride, const StepParams p) {
+// Pull A-B step from s'(t-1) in one launch: gather f(t) through the index
+// table (walls: the site's own opposite slot), collide, store coalesced.
+// Every stride-th block (the first n_iolet_blocks of them) takes eight
+// iolet sites, a warp each (step_iolet_site); the others take 256 bulk sites,
+// a thread each, and leave iolet sites alone.  The iolet blocks, spread
+// through the grid, run beside the bulk blocks instead of after them.
+// WIDE: offsets within direction pairs (lattices above ~226M sites).
+template <typename S, bool WIDE>
+__global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S* __restrict__ fout,
+                                                const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
+                                                const double* __restrict__ amp, const int32_t* __restrict__ sites,
+                                                int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
+                                                const StepParams p) {
   using R = typename Real<S>::type;
   const unsigned b = blockIdx.x, j = b / stride;
   if (b % stride == 0 && j < n_iolet_blocks) {
@@ -153,14 +116,21 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step32(const S* __restrict__ fin, 
   bool iolet = false;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int32_t s = ldidx(src + (uint32_t)(i - 1) * sn + x);
-    h[i] = ldpop(fin + (s >= 0 ? (uint32_t)i * n + (uint32_t)s : (uint32_t)opp(i) * n + x));
+    const int32_t s = ldidx(idx_at<WIDE>(src, i, sn, x));
+    // fluid source: row i at s; otherwise row opp(i) at x (bounce-back; iolets: step_iolet_site)
+    h[i] = ldpop(at<WIDE>(fin, i, n, s >= 0 ? slot<WIDE>(i, n, (uint32_t)s) : slot<WIDE>(opp(i), n, x)));
     iolet |= s <= -2;
   }
   if (iolet) return;
   collide<R>(h, R(p.omega));
+  if (WIDE) {
+    stpop<S>(fout + x, h[0]);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) stpop<S>(fout + (uint32_t)i * n + x, h[i]);
+    for (int i = 1; i < Q; ++i) stpop<S>(at<WIDE>(fout, i, n, slot<WIDE>(i, n, x)), h[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) stpop<S>(fout + (uint32_t)i * n + x, h[i]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -292,34 +262,12 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
 // post-collision population into the slot it came from, where the site
 // downstream (or, across a wall or iolet, the site itself) reads it in the
 // next (even) step.  Iolet links get their boundary values from k_aa_fix.
-// The index table is read again for the store addresses (the same 72 bytes,
-// served from cache) rather than held in registers across the collision;
-// 4 resident blocks per SM measured fastest (a small spill is cheaper than
-// the lost occupancy).
-// SAME_STRIDE: the index rows are not padded (n is a multiple of 4), so one
-// row stride serves both arrays and fewer 64-bit row offsets stay live.
-template <typename S, bool SAME_STRIDE>
-__global__ void __launch_bounds__(BLOCK, 4) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
-  using R = typename Real<S>::type;
-  const int64_t n = p.n, sn = SAME_STRIDE ? p.n : p.sn;
-  const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
-  if (x >= n) return;
-  R h[Q];
-  h[0] = to_real(A[x]);
-#pragma unroll
-  for (int i = 1; i < Q; ++i) h[i] = to_real(A[aa_addr(i, __ldg(src + (int64_t)(i - 1) * sn + x), n, x)]);
-  collide<R>(h, R(p.omega));
-  stpop<S>(A + x, h[0]);
-#pragma unroll
-  for (int i = 1; i < Q; ++i) stpop<S>(A + aa_addr(i, __ldg(src + (int64_t)(i - 1) * sn + x), n, x), h[opp(i)]);
-}
-
-// The same step with 32-bit element offsets (19 x the row stride fits in 32
-// bits): the 18 slot offsets are computed once and held in registers for the
-// stores, so the index row is read only once.  Five resident blocks per SM
-// (51 registers, a few bytes of spill in FP32) measured fastest.
-template <typename S>
-__global__ void __launch_bounds__(BLOCK, 5) k_aa_odd32(S* A, const int32_t* __restrict__ src, const StepParams p) {
+// The 18 slot offsets (32-bit) are computed once and held in registers for
+// the stores, so the index row is read once.  Five resident blocks per SM
+// (48 registers, a few bytes of spill in FP32) measured fastest.  WIDE:
+// offsets within direction pairs (lattices above ~226M sites).
+template <typename S, bool WIDE>
+__global__ void __launch_bounds__(BLOCK, 5) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
   using R = typename Real<S>::type;
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
   const uint32_t x = blockIdx.x * BLOCK + threadIdx.x;
@@ -329,14 +277,15 @@ __global__ void __launch_bounds__(BLOCK, 5) k_aa_odd32(S* A, const int32_t* __re
   h[0] = to_real(A[x]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int32_t s = __ldg(src + (uint32_t)(i - 1) * sn + x);
-    off[i] = s >= 0 ? (uint32_t)opp(i) * n + (uint32_t)s : (uint32_t)i * n + x;
-    h[i] = to_real(A[off[i]]);
+    const int32_t s = __ldg(idx_at<WIDE>(src, i, sn, x));
+    // slot opp(i) of the source, or slot i of x itself across a wall or iolet
+    off[i] = s >= 0 ? slot<WIDE>(opp(i), n, (uint32_t)s) : slot<WIDE>(i, n, x);
+    h[i] = to_real(*at<WIDE>(A, i, n, off[i]));
   }
   collide<R>(h, R(p.omega));
   stpop<S>(A + x, h[0]);
 #pragma unroll
-  for (int i = 1; i < Q; ++i) stpop<S>(A + off[i], h[opp(i)]);
+  for (int i = 1; i < Q; ++i) stpop<S>(at<WIDE>(A, i, n, off[i]), h[opp(i)]);
 }
 
 // ---------------------------------------------------------------------------
@@ -558,24 +507,6 @@ __global__ void k_zero(double* p, int64_t m) {
 // ---------------------------------------------------------------------------
 // dispatch
 // ---------------------------------------------------------------------------
-// Grid of a persistent tile kernel: resident CTAs per SM x SMs, capped by
-// the number of tiles.  Cached per kernel and device.
-template <typename K>
-unsigned persistent_grid(const hlb_solver* h, K kernel) {
-  static int cache[64] = {0};
-  const int dev = h->device >= 0 && h->device < 64 ? h->device : 0;
-  if (!cache[dev]) {
-    int sms = 0, occ = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // prefer the largest shared-memory carveout: these kernels stage index tiles
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, TILE, 0);
-    cache[dev] = (sms > 0 ? sms : 1) * (occ > 0 ? occ : 1);
-  }
-  const int64_t ntiles = (h->n + TILE - 1) / TILE;
-  return (unsigned)(ntiles < cache[dev] ? ntiles : cache[dev]);
-}
-
 template <template <typename> class F, typename... A>
 cudaError_t dispatch(int precision, A... a) {
   switch (precision) {
@@ -592,16 +523,12 @@ struct StepOp {
   static cudaError_t run(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
                          cudaStream_t s) {
     StepParams p = h->params(tb);
-    if (gather && h->off32) {
+    if (gather) {
       const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // 8 warps (sites) per block
       const unsigned grid = gi + grid_for(h->n);
-      k_step32<S><<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
-                                         h->n_iolet_sites, gi, gi ? grid / gi : 1, p);
-    } else if (gather) {
-      k_step<S><<<persistent_grid(h, k_step<S>), TILE, 0, s>>>((const S*)fin, (S*)fout, h->d_src, p, h->d_err);
-      if (h->n_iolet_sites > 0)
-        k_step_iolet<S><<<(unsigned)((h->n_iolet_sites + 7) / 8), 256, 0, s>>>(
-            (const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites, h->n_iolet_sites, p);
+      auto kernel = h->off32 ? k_step<S, false> : k_step<S, true>;
+      kernel<<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+                                    h->n_iolet_sites, gi, gi ? grid / gi : 1, p);
     } else {
       k_step_local<S><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, p);
     }
@@ -633,12 +560,7 @@ struct AAOp {
   static cudaError_t run(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
     StepParams p = h->params(t);
     if (odd)
-      if (h->off32)
-        k_aa_odd32<S><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
-      else if (h->sn == h->n)
-        k_aa_odd<S, true><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
-      else
-        k_aa_odd<S, false><<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
+      (h->off32 ? k_aa_odd<S, false> : k_aa_odd<S, true>)<<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
     else
       aa_even<S>(h, (S*)A, p, s);
     if (h->n_iolet_sites > 0) {

@@ -60,7 +60,6 @@ struct hlb_solver {
   float* d_normal = nullptr;          // [3][n] or null
   float* d_stage = nullptr;           // [5][n] staging for host readback
   double* d_red = nullptr;            // reduction scratch
-  int* d_err = nullptr;               // set by device code when a bounded wait runs out
   double* d_lflux = nullptr;          // [n_links] mass let in by each iolet link in the last AA step
   int32_t* d_iolet_sites = nullptr;   // sites with at least one iolet link (AA boundary fix-up)
   int64_t* d_ioff = nullptr;          // [n_iolets + 1] ranges of d_ilist per iolet
@@ -78,7 +77,6 @@ struct hlb_solver {
 // thread-local error text
 int hlb_fail(int code, const std::string& msg);
 // HLB_OK, or HLB_ERR_CUDA if a kernel recorded a timed-out wait (synchronises).
-int hlb_check_device_error(hlb_solver* h);
 int hlb_cuda_fail(cudaError_t e, const char* where);
 
 // ---- launchers (hlb_forward.cu) ----
