@@ -109,7 +109,7 @@ StepParams hlb_solver::params(int64_t tb) const {
 namespace {
 
 struct Layout {
-  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, ioff = 0,
+  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, icode = 0, ioff = 0,
          ilist = 0, mon = 0, total = 0;
   int64_t n_links = 0;
   int32_t n_groups = 0;
@@ -188,6 +188,7 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.red = off; off += align_up(sizeof(double) * (size_t)hlb_reduce_slots(n, L->n_iolets));
   y.lflux = off; off += align_up(sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.isites = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(n_iolet_sites, 1));
+  y.icode = off; off += align_up(sizeof(int32_t) * 18 * (size_t)std::max<int64_t>(n_iolet_sites, 1));
   y.ioff = off; off += align_up(sizeof(int64_t) * (size_t)(L->n_iolets + 1));
   y.ilist = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(y.n_links, 1));  // >= sites per iolet
   y.mon = off; off += align_up(sizeof(double) * 2 * (size_t)std::max(L->n_iolets, 1));
@@ -268,6 +269,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->red_slots = hlb_reduce_slots(n, h->n_iolets);
   h->d_lflux = (double*)(base + y.lflux);
   h->d_iolet_sites = (int32_t*)(base + y.isites);
+  h->d_icode = (int32_t*)(base + y.icode);
   h->d_ioff = (int64_t*)(base + y.ioff);
   h->d_ilist = (int32_t*)(base + y.ilist);
   h->d_mon = (double*)(base + y.mon);
@@ -360,6 +362,12 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
     e = cudaMemcpyAsync(h->d_red + nb, begin.data(), sizeof(int64_t) * begin.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nis > 0)
     e = cudaMemcpyAsync(h->d_iolet_sites, isites.data(), sizeof(int32_t) * (size_t)nis, cudaMemcpyHostToDevice, st);
+  // compact index codes of the iolet sites (the library's own re-coded table)
+  std::vector<int32_t> icode((size_t)18 * (size_t)nis);
+  for (int i = 1; i < Q; ++i)
+    for (int64_t q = 0; q < nis; ++q) icode[(size_t)(i - 1) * nis + q] = src[(size_t)(i - 1) * sn + isites[q]];
+  if (e == cudaSuccess && nis > 0)
+    e = cudaMemcpyAsync(h->d_icode, icode.data(), sizeof(int32_t) * icode.size(), cudaMemcpyHostToDevice, st);
   // sites of each iolet (a link to it), ascending, as ranges of one list
   std::vector<std::vector<int32_t>> per_io((size_t)h->n_iolets);
   for (int32_t x : isites) {

@@ -219,8 +219,10 @@ __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, 
 // step, and in the slot it read direction i from after an odd step; an iolet
 // link's slot is slot i of x in both cases.  Boundary values use the moments
 // of these stored values, as the A-B gather does.
+// icode[(i - 1) nsites + q] is the index code of direction i at iolet site
+// q, a compact copy of the table's rows (coalesced here, scattered there).
 template <typename S, bool ODD>
-__global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict__ src,
+__global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict__ icode,
                                                 const LinkRec* __restrict__ links, const double* __restrict__ amp,
                                                 const int32_t* __restrict__ sites, int64_t nsites,
                                                 const StepParams p, double* __restrict__ lflux) {
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
   int32_t code[Q];
   code[0] = 0;
 #pragma unroll
-  for (int i = 1; i < Q; ++i) code[i] = src[(int64_t)(i - 1) * p.sn + x];
+  for (int i = 1; i < Q; ++i) code[i] = icode[(int64_t)(i - 1) * nsites + q];
   R v[Q];  // v[i] = s'_ibar(x), the value in the slot the link of direction i reads
 #pragma unroll
   for (int i = 0; i < Q; ++i)
@@ -246,15 +248,21 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
   }
   const R rho = R(1) + d;
   const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
+  // all loads first, stores after: the record and amplitude loads of the 18
+  // directions can then be in flight together
+  R val[Q];
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const bool io = code[i] <= -2;
     const LinkRec L = links[io ? -code[i] - 2 : 0];  // record 0 exists whenever a site has an iolet link
     const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
-    if (!io) continue;
-    const R val = lane_iolet_value<R>(i, L, v[i], rho, ux, uy, uz, a, p);
-    lflux[-code[i] - 2] = (double)val - (double)v[i];
-    A[(int64_t)i * n + x] = from_real<S>(val);
+    val[i] = io ? lane_iolet_value<R>(i, L, v[i], rho, ux, uy, uz, a, p) : R(0);
+  }
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (code[i] > -2) continue;
+    lflux[-code[i] - 2] = (double)val[i] - (double)v[i];
+    A[(int64_t)i * n + x] = from_real<S>(val[i]);
   }
 }
 
@@ -566,10 +574,10 @@ struct AAOp {
     if (h->n_iolet_sites > 0) {
       const unsigned g = (unsigned)((h->n_iolet_sites + 127) / 128);  // one thread per iolet site
       if (odd)
-        k_aa_fix<S, true><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+        k_aa_fix<S, true><<<g, 128, 0, s>>>((S*)A, h->d_icode, h->d_links, h->d_amp, h->d_iolet_sites,
                                             h->n_iolet_sites, p, h->d_lflux);
       else
-        k_aa_fix<S, false><<<g, 128, 0, s>>>((S*)A, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
+        k_aa_fix<S, false><<<g, 128, 0, s>>>((S*)A, h->d_icode, h->d_links, h->d_amp, h->d_iolet_sites,
                                              h->n_iolet_sites, p, h->d_lflux);
     }
     return cudaGetLastError();

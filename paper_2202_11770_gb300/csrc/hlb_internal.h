@@ -62,6 +62,7 @@ struct hlb_solver {
   double* d_red = nullptr;            // reduction scratch
   double* d_lflux = nullptr;          // [n_links] mass let in by each iolet link in the last AA step
   int32_t* d_iolet_sites = nullptr;   // sites with at least one iolet link (AA boundary fix-up)
+  int32_t* d_icode = nullptr;         // [18][n_iolet_sites] their index codes, compact
   int64_t* d_ioff = nullptr;          // [n_iolets + 1] ranges of d_ilist per iolet
   int32_t* d_ilist = nullptr;         // sites with a link to iolet k, ascending, iolet by iolet
   double* d_mon = nullptr;            // [2][n_iolets] monitor outputs
