@@ -62,6 +62,12 @@ def _load():
         lib.ora_flux.argtypes = [_P, _D]
         lib.ora_wave_value.argtypes = [_P, C.c_int, C.c_double]
         lib.ora_wave_value.restype = C.c_double
+        lib.ora_set_windkessel.argtypes = [_P, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                           C.c_double]
+        lib.ora_windkessel_rho.argtypes = [_P, C.c_int]
+        lib.ora_windkessel_rho.restype = C.c_double
+        lib.ora_windkessel_rho_c.argtypes = [_P, C.c_int]
+        lib.ora_windkessel_rho_c.restype = C.c_double
         lib.ora_macros.argtypes = [_P, _D, _D, _D, C.POINTER(C.c_float)]
         lib.ora_objective.argtypes = [_P, C.c_int64, C.c_int64, _I64, _D, _D]
         lib.ora_objective.restype = C.c_double
@@ -202,6 +208,20 @@ class Oracle:
         out = np.zeros(max(self.nio, 1), np.float64)
         self._lib.ora_flux(self._h, _ptr(out, C.c_double))
         return out[: self.nio]
+
+    def set_windkessel(self, k: int, Rp: float, C: float, Rd: float, rho_d: float = 1.0, rho_c0=None):
+        """Pressure iolet k as a three-element Windkessel outlet (see oracle.c)."""
+        rc = self._lib.ora_set_windkessel(self._h, int(k), float(Rp), float(C), float(Rd), float(rho_d),
+                                          float(rho_d if rho_c0 is None else rho_c0))
+        if rc:
+            raise ValueError(self._lib.ora_last_error().decode())
+
+    def windkessel_rho(self, k: int) -> float:
+        """Ghost density outlet k used in the last step."""
+        return float(self._lib.ora_windkessel_rho(self._h, int(k)))
+
+    def windkessel_rho_c(self, k: int) -> float:
+        return float(self._lib.ora_windkessel_rho_c(self._h, int(k)))
 
     def wave_value(self, k: int, t: float) -> float:
         """Waveform of iolet k at time t (velocity: the w(t) multiplying the

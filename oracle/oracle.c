@@ -97,11 +97,25 @@ static double wave_at(const wave_t* w, double t) {
 }
 
 /* ---------------- oracle object ---------------- */
+/* Three-element Windkessel outlet (resistance Rp, compliance C, resistance
+ * Rd to a distal density rho_d), coupled explicitly: the ghost density used
+ * to produce f(m+1) is rho_c(m) + Rp q(m), with q(m) the volumetric outflow
+ * (minus the mass flux) of the step that produced f(m); after that step
+ * rho_c(m+1) = rho_c(m) + (q(m+1) - (rho_c(m) - rho_d) / Rd) / C.  C = 0
+ * means no compliance: ghost density rho_d + (Rp + Rd) q(m). */
+typedef struct {
+  int on;
+  double Rp, C, Rd, rho_d;
+  double rho_c, q;   /* state: compliance density, outflow of the last step */
+  double rho_used;   /* ghost density used in the last step */
+} wk_t;
+
 typedef struct {
   int kind; /* 0 velocity, 1 pressure */
   double c[3], nrm[3], R;
   int ngroups, goff;
   wave_t wave;
+  wk_t wk;
 } iolet_t;
 
 typedef struct {
@@ -271,6 +285,25 @@ int ora_set_velocity(ora_t* o, int k, const double* amps, int ngroups, int kind,
   for (int g = 0; g < ngroups; ++g) o->amp[o->io[k].goff + g] = amps[g];
   return set_wave(&o->io[k].wave, kind, mean, rel, period, phase, nsamp, samp);
 }
+/* Pressure iolet k becomes a Windkessel outlet (Rp, C, Rd >= 0) with
+ * compliance density rho_c0 and no outflow history.  With C > 0 the
+ * explicit update of rho_c multiplies its distance to the fixed point by
+ * 1 - 1/(Rd C) per step, so Rd C >= 1 is required (no overshoot). */
+int ora_set_windkessel(ora_t* o, int k, double Rp, double C, double Rd, double rho_d, double rho_c0) {
+  if (k < 0 || k >= o->nio || o->io[k].kind != 1) return fail("not a pressure iolet");
+  if (!(Rp >= 0) || !(C >= 0) || !(Rd >= 0) || (C > 0 && !(Rd * C >= 1))) return fail("bad Windkessel parameters");
+  wk_t* m = &o->io[k].wk;
+  m->on = 1; m->Rp = Rp; m->C = C; m->Rd = Rd; m->rho_d = rho_d;
+  m->rho_c = C > 0 ? rho_c0 : rho_d;
+  m->q = 0;
+  m->rho_used = NAN;
+  return 0;
+}
+/* Ghost density iolet k used in the last step (Windkessel outlets), and the
+ * compliance density now. */
+double ora_windkessel_rho(const ora_t* o, int k) { return o->io[k].wk.rho_used; }
+double ora_windkessel_rho_c(const ora_t* o, int k) { return o->io[k].wk.rho_c; }
+
 /* Value of iolet k's waveform at time t (test access to wave_at). */
 double ora_wave_value(const ora_t* o, int k, double t) {
   if (k < 0 || k >= o->nio) return NAN;
@@ -280,6 +313,7 @@ double ora_wave_value(const ora_t* o, int k, double t) {
 int ora_set_pressure(ora_t* o, int k, int kind, double mean, double rel, double period,
                      double phase, int nsamp, const double* samp) {
   if (k < 0 || k >= o->nio || o->io[k].kind != 1) return fail("not a pressure iolet");
+  o->io[k].wk.on = 0;
   return set_wave(&o->io[k].wave, kind, mean, rel, period, phase, nsamp, samp);
 }
 
@@ -319,7 +353,10 @@ void ora_init_equilibrium(ora_t* o, double rho0, const double* u0) {
   double zero[3] = {0, 0, 0};
   for (int64_t x = 0; x < o->n; ++x) ora_feq(rho0, u0 ? &u0[3 * x] : zero, &o->f[x * Q]);
   o->t = 0;
-  for (int k = 0; k < o->nio; ++k) o->flux[k] = 0;
+  for (int k = 0; k < o->nio; ++k) {
+    o->flux[k] = 0;
+    o->io[k].wk.q = 0;  /* no outflow history; the compliance density is kept */
+  }
 }
 
 /* One time step: collide every site, push to neighbours, apply BCs. */
@@ -327,7 +364,14 @@ static void step_once(ora_t* o) {
   const int64_t n = o->n;
   const double t = (double)o->t;
   double wk[256];
-  for (int k = 0; k < o->nio && k < 256; ++k) wk[k] = wave_at(&o->io[k].wave, t);
+  for (int k = 0; k < o->nio && k < 256; ++k) {
+    const wk_t* m = &o->io[k].wk;
+    if (m->on)
+      wk[k] = m->C > 0 ? m->rho_c + m->Rp * m->q : m->rho_d + (m->Rp + m->Rd) * m->q;
+    else
+      wk[k] = wave_at(&o->io[k].wave, t);
+    o->io[k].wk.rho_used = wk[k];
+  }
   for (int k = 0; k < o->nio; ++k) o->flux[k] = 0;
   for (int64_t x = 0; x < n; ++x) {
     const double* f = &o->f[x * Q];
@@ -375,6 +419,12 @@ static void step_once(ora_t* o) {
   o->f = o->fn;
   o->fn = tmp;
   o->t += 1;
+  for (int k = 0; k < o->nio; ++k) {
+    wk_t* m = &o->io[k].wk;
+    if (!m->on) continue;
+    m->q = -o->flux[k];
+    if (m->C > 0) m->rho_c += (m->q - (m->rho_c - m->rho_d) / m->Rd) / m->C;
+  }
 }
 
 void ora_step(ora_t* o, int64_t nsteps) {
