@@ -67,10 +67,10 @@ ELEM = {"fp32": 4, "bf16": 2, "fp16": 2, "fp64": 8}
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": "72ecef0861532b80",
+TRAFFIC = {"sha": "2fb1d5615afba6c5",
            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site tree
-           "bytes_per_site": {"k_aa_odd": (2960286208 + 1488272384) / 20000864,
-                              "k_step": (3050513408 + 1482803968) / 20000864}}
+           "bytes_per_site": {"k_aa_odd": (2960247552 + 1488028160) / 20000864,
+                              "k_step": (3050510848 + 1482741760) / 20000864}}
 
 
 def kernel_sha() -> str:
