@@ -180,8 +180,29 @@ int hlb_set_velocity_waveform(hlb_solver* h, int32_t k, const double* amp, int32
                               const hlb_waveform* w);
 
 /* Pressure iolet k (Section 2.3.2, Eq. 7): ghost density rho(t) = w(t)
- * (= p(t)/cs^2).  HLB_ERR_ARG if k is not a pressure iolet. */
+ * (= p(t)/cs^2).  HLB_ERR_ARG if k is not a pressure iolet.  Turns a
+ * Windkessel outlet back into a waveform outlet. */
 int hlb_set_pressure(hlb_solver* h, int32_t k, const hlb_waveform* w);
+
+/* Pressure iolet k as a three-element Windkessel outlet: the downstream
+ * resistance model that the paper's Section 7 names as future work (not part
+ * of its method).  The ghost density becomes state of the device:
+ *   ghost density for the next step = rho_c + Rp q,
+ *   rho_c <- rho_c + (q - (rho_c - rho_d) / Rd) / C   after each step,
+ * q being the outflow (minus the mass flux of hlb_reduce) of the step that
+ * produced the current state; C = 0 is a pure resistance, ghost density
+ * rho_d + (Rp + Rd) q.  The coupling is explicit (one step of lag) and runs
+ * one extra small kernel per step.  rho_c starts at rho_c0 (C > 0) and the
+ * outflow history at 0; hlb_init_equilibrium clears the history again.
+ * Densities are lattice densities (pressure = rho / 3).  HLB_ERR_ARG if k
+ * is not a pressure iolet, a parameter is negative, rho_d or rho_c0 is not
+ * positive, or C > 0 with Rd C < 1 (the explicit update would overshoot).
+ * hlb_adjoint_run refuses a solver with Windkessel outlets. */
+int hlb_set_windkessel(hlb_solver* h, int32_t k, double Rp, double C, double Rd, double rho_d, double rho_c0);
+
+/* Model state of Windkessel outlet k (synchronises): the ghost density the
+ * next boundary evaluation uses, rho_c and the last outflow q (any NULL). */
+int hlb_windkessel_state(hlb_solver* h, int32_t k, double* rho_ghost, double* rho_c, double* q);
 
 /* Set f = f^eq(rho0, u0) everywhere and t = 0 (Section 3.1 step 1).  u0 is
  * float [3][N] (host or device per `where`) or NULL for u = 0. */

@@ -637,6 +637,7 @@ extern "C" int hlb_adjoint_run(hlb_solver* h, int64_t nsteps, const hlb_objectiv
                                double* J, double* dtau, double* damp) {
   int rc = check_objective(h, nsteps, obj);
   if (rc) return rc;
+  if (h->any_wk()) return hlb_fail(HLB_ERR_ARG, "the adjoint does not differentiate Windkessel outlets");
   AdjLayout y = adj_layout(h, nsteps, obj->n_probe);
   if (!ws || ((uintptr_t)ws & 255)) return hlb_fail(HLB_ERR_WS, "adjoint workspace missing or not 256-byte aligned");
   if (ws_bytes < y.total)

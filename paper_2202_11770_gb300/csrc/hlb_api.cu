@@ -93,6 +93,9 @@ StepParams hlb_solver::params(int64_t tb) const {
   p.n_iolets = n_iolets;
   p.ladd_rho_one = ladd_rho_one;
   p.ghost_full_u = ghost_full_u;
+  p.ioval = d_ioval;
+  for (int k = 0; k < n_iolets; ++k)
+    if (k < (int)wk_on.size() && wk_on[k]) p.coupled[k >> 6] |= 1ull << (k & 63);
   for (int k = 0; k < n_iolets; ++k) {
     p.io[k].nx = iolets[k].normal[0];
     p.io[k].ny = iolets[k].normal[1];
@@ -110,7 +113,8 @@ namespace {
 
 struct Layout {
   size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, icode = 0, ioff = 0,
-         ilist = 0, mon = 0, total = 0;
+         ilist = 0, mon = 0, wkpar = 0, wkstate = 0,
+         ioval = 0, iovnext = 0, total = 0;
   int64_t n_links = 0;
   int32_t n_groups = 0;
 };
@@ -192,6 +196,10 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.ioff = off; off += align_up(sizeof(int64_t) * (size_t)(L->n_iolets + 1));
   y.ilist = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(y.n_links, 1));  // >= sites per iolet
   y.mon = off; off += align_up(sizeof(double) * 2 * (size_t)std::max(L->n_iolets, 1));
+  y.wkpar = off; off += align_up(sizeof(double) * 4 * (size_t)std::max(L->n_iolets, 1));
+  y.wkstate = off; off += align_up(sizeof(double) * 2 * (size_t)std::max(L->n_iolets, 1));
+  y.ioval = off; off += align_up(sizeof(double) * (size_t)std::max(L->n_iolets, 1));
+  y.iovnext = off; off += align_up(sizeof(double) * (size_t)std::max(L->n_iolets, 1));
   y.total = off;
   return y;
 }
@@ -273,6 +281,11 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->d_ioff = (int64_t*)(base + y.ioff);
   h->d_ilist = (int32_t*)(base + y.ilist);
   h->d_mon = (double*)(base + y.mon);
+  h->d_wkpar = (double*)(base + y.wkpar);
+  h->d_wkstate = (double*)(base + y.wkstate);
+  h->d_ioval = (double*)(base + y.ioval);
+  h->d_iovnext = (double*)(base + y.iovnext);
+  h->wk_on.assign((size_t)h->n_iolets, 0);
   h->n_iolet_sites = nis;
 
   // link records sorted by (iolet, group, site, direction)
@@ -452,6 +465,44 @@ extern "C" int hlb_set_pressure(hlb_solver* h, int32_t k, const hlb_waveform* w)
   int rc = parse_wave(w, &hw);
   if (rc) return rc;
   h->wave[k] = hw;
+  h->wk_on[k] = 0;
+  return HLB_OK;
+}
+
+extern "C" int hlb_set_windkessel(hlb_solver* h, int32_t k, double Rp, double C, double Rd, double rho_d,
+                                  double rho_c0) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (k < 0 || k >= h->n_iolets || h->iolets[k].kind != HLB_PRESSURE)
+    return hlb_fail(HLB_ERR_ARG, "not a pressure iolet");
+  if (!(Rp >= 0) || !(C >= 0) || !(Rd >= 0) || (C > 0 && !(Rd * C >= 1)) || !(rho_d > 0) ||
+      (C > 0 && !(rho_c0 > 0)))
+    return hlb_fail(HLB_ERR_ARG, "Windkessel needs Rp, C, Rd >= 0, Rd C >= 1 when C > 0, positive densities");
+  const double par[4] = {Rp, C, Rd, rho_d};
+  const double rho_c = C > 0 ? rho_c0 : rho_d;
+  const double state[2] = {rho_c, 0.0};
+  const double val = rho_c - 1.0;  // ghost density before any outflow: rho_c + Rp * 0
+  CUDA_TRY(cudaMemcpyAsync(h->d_wkpar + 4 * k, par, sizeof par, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_wkstate + 2 * k, state, sizeof state, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_ioval + k, &val, sizeof val, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_iovnext + k, &val, sizeof val, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->wk_on[k] = 1;
+  return HLB_OK;
+}
+
+extern "C" int hlb_windkessel_state(hlb_solver* h, int32_t k, double* rho_ghost, double* rho_c, double* q) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (k < 0 || k >= h->n_iolets || !h->wk_on[k]) return hlb_fail(HLB_ERR_ARG, "not a Windkessel outlet");
+  double state[2], val;
+  CUDA_TRY(cudaMemcpyAsync(state, h->d_wkstate + 2 * k, sizeof state, cudaMemcpyDeviceToHost, h->stream));
+  // the ghost density that produces the next state: AA has already applied
+  // the current one, pull A-B applies it at the next gather
+  const double* g = h->scheme == HLB_AA ? h->d_ioval : h->d_iovnext;
+  CUDA_TRY(cudaMemcpyAsync(&val, g + k, sizeof val, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (rho_ghost) *rho_ghost = 1.0 + val;
+  if (rho_c) *rho_c = state[0];
+  if (q) *q = state[1];
   return HLB_OK;
 }
 
@@ -464,6 +515,7 @@ extern "C" int hlb_init_equilibrium(hlb_solver* h, double rho0, const float* u0,
     du = h->d_stage;
   }
   CUDA_TRY(hlb_launch_init(h, h->f[0], rho0, du, h->stream));
+  if (h->any_wk()) CUDA_TRY(hlb_launch_wk_reset(h, h->stream));
   h->cur = 0;
   h->phase = HLB_READ_LOCAL;
   h->t = 0;
@@ -480,10 +532,13 @@ extern "C" int hlb_step(hlb_solver* h, int64_t nsteps) {
       // even step from f(t) in place, odd step from the swapped buffer
       const bool odd = h->phase == HLB_READ_GATHER_AA;
       CUDA_TRY(hlb_launch_aa(h, h->f[0], odd, h->t, h->stream));
+      if (h->any_wk()) CUDA_TRY(hlb_launch_wk_update(h, nullptr, h->t, false, h->stream));
       h->phase = odd ? HLB_READ_LOCAL : HLB_READ_GATHER_AA;
     } else {
       const bool gather = h->phase == HLB_READ_GATHER_AB;
       CUDA_TRY(hlb_launch_step(h, h->f[h->cur], h->f[h->cur ^ 1], gather, h->t - 1, h->stream));
+      // outflow into f(t+1) = G(s'(t)): the new s'(t) with the ghost density the next gather uses
+      if (h->any_wk()) CUDA_TRY(hlb_launch_wk_update(h, h->f[h->cur ^ 1], h->t, gather, h->stream));
       h->cur ^= 1;
       h->phase = HLB_READ_GATHER_AB;
     }

@@ -107,8 +107,17 @@ struct StepParams {
   int32_t ladd_rho_one;
   int32_t ghost_full_u;
   int32_t pad;
+  uint64_t coupled[MAX_IOLETS / 64];  // bit k: iolet k's value lives in ioval[k] (Windkessel outlet)
+  const double* ioval;                // device, [n_iolets]: rho - 1 of coupled outlets
   IoletParam io[MAX_IOLETS];
 };
+static_assert(MAX_IOLETS % 64 == 0, "coupling mask words");
+
+// Boundary value of iolet k for this launch: the host waveform, or for a
+// Windkessel outlet the ghost density the device-side model last produced.
+__device__ __forceinline__ double io_val(const StepParams& p, int k) {
+  return ((p.coupled[k >> 6] >> (k & 63)) & 1ull) ? p.ioval[k] : p.io[k].val;
+}
 
 // ---------------------------------------------------------------------------
 // Moments and equilibrium in shifted form.
@@ -228,7 +237,7 @@ __device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int
     const IoletParam iop = p.io[L.iolet];
     if (L.kind == 0) {
       R rho = p.ladd_rho_one ? R(1) : rho_s;
-      h[i] += R(L.coef) * rho * R(a) * R(iop.val);
+      h[i] += R(L.coef) * rho * R(a) * R(io_val(p, L.iolet));
     } else {
       R gx = ux, gy = uy, gz = uz;
       if (!p.ghost_full_u) {
@@ -237,7 +246,7 @@ __device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int
         gy = un * R(iop.ny);
         gz = un * R(iop.nz);
       }
-      R drho = R(iop.val);
+      R drho = R(io_val(p, L.iolet));
       R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
       h[i] = heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
     }
@@ -316,7 +325,7 @@ __device__ __forceinline__ R lane_iolet_value(int i, const LinkRec& L, R out, R 
   const IoletParam iop = p.io[L.iolet];
   if (L.kind == 0) {
     R rho = p.ladd_rho_one ? R(1) : rho_s;
-    return out + R(L.coef) * rho * R(a) * R(iop.val);
+    return out + R(L.coef) * rho * R(a) * R(io_val(p, L.iolet));
   }
   R gx = ux, gy = uy, gz = uz;
   if (!p.ghost_full_u) {
@@ -325,7 +334,7 @@ __device__ __forceinline__ R lane_iolet_value(int i, const LinkRec& L, R out, R 
     gy = un * R(iop.ny);
     gz = un * R(iop.nz);
   }
-  R drho = R(iop.val);
+  R drho = R(io_val(p, L.iolet));
   R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
   return lane_heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
 }

@@ -196,7 +196,7 @@ __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, 
   const IoletParam io = p.io[L.iolet];
   if (L.kind == 0) {
     R r = p.ladd_rho_one ? R(1) : rho;
-    return out + R(L.coef) * r * R(amp[L.group]) * R(io.val);
+    return out + R(L.coef) * r * R(amp[L.group]) * R(io_val(p, L.iolet));
   }
   R gx = ux, gy = uy, gz = uz;
   if (!p.ghost_full_u) {
@@ -205,7 +205,7 @@ __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, 
     gy = un * R(io.ny);
     gz = un * R(io.nz);
   }
-  R drho = R(io.val);
+  R drho = R(io_val(p, L.iolet));
   R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
   return heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
 }
@@ -643,6 +643,101 @@ __global__ void __launch_bounds__(256) k_iolet_monitor(const S* __restrict__ fin
   }
 }
 
+// Windkessel outlets after a step (block k = iolet k; other iolets return).
+// q = -(mass that enters through outlet k to produce the current state f):
+//  * AA: the fix-up pass has just written f's boundary values with ioval[k]
+//    and recorded the per-link masses; q is their sum.
+//  * A-B: f's boundary values are applied by the next gather.  That gather
+//    uses the value computed one update earlier (iovnext[k]), which `shift`
+//    moves into ioval[k]; q is then recomputed from the post-collision state
+//    `fin` with it, exactly as the gather will see it.
+// Then rho_c <- rho_c + (q - (rho_c - rho_d) / Rd) / C and the next ghost
+// density rho_c + Rp q (C = 0: rho_d + (Rp + Rd) q) goes to ioval[k] (AA) or
+// iovnext[k] (A-B), minus 1.
+template <typename S, bool AA>
+__global__ void __launch_bounds__(BLOCK) k_wk_update(const S* __restrict__ fin, const LinkRec* __restrict__ links,
+                                                     const double* __restrict__ amp, const StepParams p,
+                                                     const int64_t* __restrict__ begin,
+                                                     const double* __restrict__ lflux,
+                                                     const double* __restrict__ par, double* __restrict__ state,
+                                                     double* ioval, double* __restrict__ iovnext, int shift) {
+  using R = typename Real<S>::type;
+  __shared__ double sh[BLOCK / 32];
+  const int k = blockIdx.x;
+  if (!((p.coupled[k >> 6] >> (k & 63)) & 1ull)) return;  // uniform per block
+  if (!AA && shift) {
+    if (threadIdx.x == 0) ioval[k] = iovnext[k];
+    __syncthreads();  // io_val(p, k) below reads it (p.ioval == ioval)
+  }
+  const int64_t n = p.n;
+  double acc = 0;
+  for (int64_t r = begin[k] + threadIdx.x; r < begin[k + 1]; r += BLOCK) {
+    if (AA) {
+      acc += lflux[r];
+    } else {
+      const LinkRec L = links[r];
+      const int64_t x = L.site;
+      R own[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) own[i] = ldpop(fin + (int64_t)i * n + x);
+      const Macro<R> ms = moments<R>(own);
+      const int j = L.dir;
+      R out = R(0), val = R(0);
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if (i == opp(j)) out = own[i];
+#pragma unroll
+      for (int i = 1; i < Q; ++i)
+        if (i == j) val = iolet_value<R>(i, L, out, ms.rho, ms.ux, ms.uy, ms.uz, amp, p);
+      acc += (double)val - (double)out;
+    }
+  }
+  const double flux = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    const double Rp = par[4 * k], C = par[4 * k + 1], Rd = par[4 * k + 2], rho_d = par[4 * k + 3];
+    const double q = -flux;
+    double rho_c = state[2 * k], ghost;
+    if (C > 0) {
+      rho_c += (q - (rho_c - rho_d) / Rd) / C;
+      ghost = rho_c + Rp * q;
+    } else {
+      ghost = rho_d + (Rp + Rd) * q;
+    }
+    state[2 * k] = rho_c;
+    state[2 * k + 1] = q;
+    (AA ? ioval : iovnext)[k] = ghost - 1.0;
+  }
+}
+
+// Windkessel outlets at initialisation: no outflow history.
+__global__ void k_wk_reset(int32_t n_iolets, const StepParams p, const double* __restrict__ par,
+                           double* __restrict__ state, double* __restrict__ ioval, double* __restrict__ iovnext) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_iolets || !((p.coupled[k >> 6] >> (k & 63)) & 1ull)) return;
+  const double C = par[4 * k + 1], rho_d = par[4 * k + 3];
+  if (!(C > 0)) state[2 * k] = rho_d;
+  state[2 * k + 1] = 0.0;
+  ioval[k] = iovnext[k] = state[2 * k] - 1.0;
+}
+
+template <typename S>
+struct WkOp {
+  static cudaError_t run(const hlb_solver* h, const void* fin, int64_t tb, bool shift, cudaStream_t s) {
+    StepParams p = h->params(tb);
+    const int64_t nb = grid_for(h->n);
+    const int64_t* begin = (const int64_t*)(h->d_red + nb);  // link ranges stored after the reduction partials
+    if (h->scheme == HLB_AA)
+      k_wk_update<S, true><<<(unsigned)h->n_iolets, BLOCK, 0, s>>>(nullptr, h->d_links, h->d_amp, p, begin,
+                                                                   h->d_lflux, h->d_wkpar, h->d_wkstate,
+                                                                   h->d_ioval, h->d_iovnext, 0);
+    else
+      k_wk_update<S, false><<<(unsigned)h->n_iolets, BLOCK, 0, s>>>((const S*)fin, h->d_links, h->d_amp, p,
+                                                                    begin, nullptr, h->d_wkpar, h->d_wkstate,
+                                                                    h->d_ioval, h->d_iovnext, shift ? 1 : 0);
+    return cudaGetLastError();
+  }
+};
+
 template <typename S>
 struct MonitorOp {
   static cudaError_t run(const hlb_solver* h, const void* fin, int mode, int64_t tb, double* out, cudaStream_t s) {
@@ -715,6 +810,15 @@ cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cud
 cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, int mode, int64_t tb, float* rho, float* u,
                               float* wss, cudaStream_t s) {
   return dispatch<MacroOp>(h->precision, h, fin, mode, tb, rho, u, wss, s);
+}
+cudaError_t hlb_launch_wk_update(const hlb_solver* h, const void* fin, int64_t tb, bool shift, cudaStream_t s) {
+  return dispatch<WkOp>(h->precision, h, fin, tb, shift, s);
+}
+cudaError_t hlb_launch_wk_reset(const hlb_solver* h, cudaStream_t s) {
+  StepParams p = h->params(h->t);
+  k_wk_reset<<<(unsigned)((h->n_iolets + 127) / 128), 128, 0, s>>>(h->n_iolets, p, h->d_wkpar, h->d_wkstate,
+                                                                   h->d_ioval, h->d_iovnext);
+  return cudaGetLastError();
 }
 cudaError_t hlb_launch_monitor(const hlb_solver* h, const void* fin, int mode, int64_t tb, double* out,
                                cudaStream_t s) {

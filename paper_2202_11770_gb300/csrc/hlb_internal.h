@@ -66,6 +66,18 @@ struct hlb_solver {
   int64_t* d_ioff = nullptr;          // [n_iolets + 1] ranges of d_ilist per iolet
   int32_t* d_ilist = nullptr;         // sites with a link to iolet k, ascending, iolet by iolet
   double* d_mon = nullptr;            // [2][n_iolets] monitor outputs
+  // Windkessel outlets: host flags, device parameters, model state and the
+  // ghost densities the kernels read (io_val)
+  std::vector<int> wk_on;             // per iolet
+  double* d_wkpar = nullptr;          // [n_iolets][4] Rp, C, Rd, rho_d
+  double* d_wkstate = nullptr;        // [n_iolets][2] rho_c, q (outflow of the last step)
+  double* d_ioval = nullptr;          // [n_iolets] ghost density - 1 the kernels read (io_val)
+  double* d_iovnext = nullptr;        // [n_iolets] pull A-B: the one after it (boundaries lag a step)
+  bool any_wk() const {
+    for (int v : wk_on)
+      if (v) return true;
+    return false;
+  }
   int64_t n_iolet_sites = 0;
   int64_t red_slots = 0;
 
@@ -89,6 +101,15 @@ cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cud
 // rho, u [3][n], wss of the current state, device outputs (any may be null).
 cudaError_t hlb_launch_macros(const hlb_solver* h, const void* fin, int mode, int64_t tb, float* rho, float* u,
                               float* wss, cudaStream_t s);
+// Windkessel outlets after a step: the outflow that produces the current
+// state (AA: recorded per-link masses; A-B: recomputed from `fin`, the
+// post-collision state the next gather reads, with parameters at tb and,
+// after `shift`, the ghost density computed one update earlier), the model
+// update, and the next ghost densities.
+cudaError_t hlb_launch_wk_update(const hlb_solver* h, const void* fin, int64_t tb, bool shift, cudaStream_t s);
+// Windkessel outlets: forget the outflow history (q = 0) and reset the ghost
+// densities to the compliance state.
+cudaError_t hlb_launch_wk_reset(const hlb_solver* h, cudaStream_t s);
 // Per-iolet max |u| (out[k]) and mean rho (out[K + k]) over the sites linked to iolet k.
 cudaError_t hlb_launch_monitor(const hlb_solver* h, const void* fin, int mode, int64_t tb, double* out,
                                cudaStream_t s);

@@ -85,6 +85,9 @@ _PROTOS = {
     "hlb_read_macros": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
     "hlb_reduce": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hlb_iolet_monitor": (C.c_int, [_P, _P, _P, _P]),
+    "hlb_set_windkessel": (C.c_int, [_P, C.c_int32, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "hlb_windkessel_state": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]),
     "hlb_get_state": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int64)]),
     "hlb_set_state": (C.c_int, [_P, _P, C.c_int32, C.c_int64]),
     "hlb_adjoint_workspace_bytes": (C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]),
@@ -333,6 +336,17 @@ class Solver:
         if rc == HLB_ERR_DIVERGED:
             raise HlbError(rc, library().hlb_last_error().decode())
         return mass, flux
+
+    def set_windkessel(self, k, Rp, C, Rd, rho_d=1.0, rho_c0=None):
+        """Pressure iolet k as a three-element Windkessel outlet (hlb_set_windkessel)."""
+        _check(self._lib.hlb_set_windkessel(self._h, int(k), float(Rp), float(C), float(Rd), float(rho_d),
+                                            float(rho_d if rho_c0 is None else rho_c0)))
+
+    def windkessel_state(self, k):
+        """(ghost density of the next step, rho_c, last outflow q) of outlet k."""
+        g, r, q = C.c_double(), C.c_double(), C.c_double()
+        _check(self._lib.hlb_windkessel_state(self._h, int(k), C.byref(g), C.byref(r), C.byref(q)))
+        return g.value, r.value, q.value
 
     def iolet_monitor(self):
         """Per iolet: (mass flux of the last step, max |u|, mean rho) over the
