@@ -208,8 +208,10 @@ int hlb_windkessel_state(hlb_solver* h, int32_t k, double* rho_ghost, double* rh
  * float [3][N] (host or device per `where`) or NULL for u = 0. */
 int hlb_init_equilibrium(hlb_solver* h, double rho0, const float* u0, int32_t where);
 
-/* Advance n >= 0 time steps (Section 3.1 steps 2-5): one fused
- * collide-stream-boundary kernel launch per step, asynchronous. */
+/* Advance n >= 0 time steps (Section 3.1 steps 2-5), asynchronously: per
+ * step one fused collide-stream-boundary kernel launch (pull A-B: iolet
+ * sites included), plus for the AA scheme the boundary pass over the iolet
+ * sites, plus one small update kernel when Windkessel outlets are set. */
 int hlb_step(hlb_solver* h, int64_t n);
 int hlb_time(const hlb_solver* h, int64_t* t);
 
