@@ -95,3 +95,16 @@ def test_amplitude_group_validation():
     opt = hemegb.hlb_options(precision=hemegb.HLB_FP32, scheme=hemegb.HLB_PULL_AB)
     with pytest.raises(hemegb.HlbError, match="group"):
         hemegb.hlb_workspace_bytes(L, opt)
+
+
+def test_lattice_size_limits():
+    """An empty lattice and one of 2^31 sites or more are rejected before any
+    array is touched (site indices are int32; 32-bit offsets cover the rest)."""
+    lib = hemegb.library()
+    opt = hemegb.hlb_options(precision=hemegb.HLB_FP32, scheme=hemegb.HLB_AA)
+    out = C.c_size_t()
+    for n in (0, -1, 1 << 31):
+        L = hemegb.hlb_lattice(n_sites=n, xyz=None, src=None, wall_normal=None, amp_group=None, n_iolets=0,
+                               iolets=None)
+        assert lib.hlb_workspace_bytes(C.byref(L), C.byref(opt), C.byref(out)) == hemegb.HLB_ERR_ARG
+        assert b"n_sites" in lib.hlb_last_error()
