@@ -67,10 +67,10 @@ ELEM = {"fp32": 4, "bf16": 2, "fp16": 2, "fp64": 8}
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": "2fb1d5615afba6c5",
+TRAFFIC = {"sha": "dd8b947313717769",
            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site tree
-           "bytes_per_site": {"k_aa_odd": (2960247552 + 1488028160) / 20000864,
-                              "k_step": (3050510848 + 1482741760) / 20000864}}
+           "bytes_per_site": {"k_aa_odd": (2960249600 + 1488131072) / 20000864,
+                              "k_step": (3050591744 + 1482896640) / 20000864}}
 
 
 def kernel_sha() -> str:
@@ -243,6 +243,8 @@ def e2e_job(lat, steps, torch):
     s = hemegb.Solver(lat_p, tau=0.55, precision="fp32")
     set_bc(s, lat_p)
     s.init_equilibrium()
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
     reads = 0
     for k in range(steps // 100):
         s.step(100)
@@ -257,7 +259,7 @@ def e2e_job(lat, steps, torch):
     d2h_step = reads * (rho_h.nbytes + u_h.nbytes) / steps + 8 * (1 + len(lat.iolets)) / steps
     del s
     torch.cuda.empty_cache()
-    return n * steps / dt / 1e6, h2d_step, d2h_step
+    return n * steps / dt / 1e6, h2d_step, d2h_step, t_create, dt
 
 
 def adjoint_ratio(steps, torch, sites=2_000_000):
@@ -430,9 +432,10 @@ def run_ours(args):
 
     e2e = None
     if not args.quick:
-        v, h2d, d2h = e2e_job(lat, args.e2e_steps, torch)
+        v, h2d, d2h, t_create, t_all = e2e_job(lat, args.e2e_steps, torch)
         e2e = {"value": v * world, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "job": f"create + init + {args.e2e_steps} steps + host readback of rho,u every 100 steps"}
+               "job": f"create + init + {args.e2e_steps} steps + host readback of rho,u every 100 steps",
+               "create_s": round(t_create, 3), "total_s": round(t_all, 3)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hlb_internal.h"
@@ -120,12 +121,48 @@ struct Layout {
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
-// Index rows are padded to a multiple of 4 entries (16 bytes) so that the
-// kernels can stage tiles of them with bulk copies.
+// Index rows are padded to a multiple of 4 entries, so every row starts on
+// a 16-byte boundary.
 int64_t row_stride(int64_t n) { return (n + 3) & ~(int64_t)3; }
 
+// An iolet link of the caller's table: site x, pull direction dir.
+struct LinkRef {
+  int32_t x;
+  int32_t dir;
+};
+
+// Checks of one direction row, run on its own thread: the first error in
+// site order, per-iolet link counts and the row's iolet links.
+struct RowCheck {
+  int code = HLB_OK;
+  const char* msg = nullptr;
+  std::vector<int64_t> per;
+  std::vector<LinkRef> links;
+};
+
+void check_row(const hlb_lattice* L, int i, RowCheck* out) {
+  const int64_t n = L->n_sites;
+  const int32_t* row = L->src + (int64_t)(i - 1) * n;
+  out->per.assign((size_t)std::max(1, (int)L->n_iolets), 0);
+  for (int64_t x = 0; x < n; ++x) {
+    const int32_t s = row[x];
+    if (s >= 0) {
+      if (s >= n) { out->code = HLB_ERR_ARG; out->msg = "src index out of range"; return; }
+    } else if (s <= -2) {
+      const int k = -s - 2;
+      if (k >= L->n_iolets) { out->code = HLB_ERR_ARG; out->msg = "link code names a missing iolet"; return; }
+      if (L->iolets[k].kind == HLB_VELOCITY && L->amp_group) {
+        const int g = L->amp_group[x];
+        if (g < 0 || g >= L->iolets[k].n_groups) { out->code = HLB_ERR_ARG; out->msg = "amplitude group out of range"; return; }
+      }
+      out->per[(size_t)k]++;
+      out->links.push_back({(int32_t)x, i});
+    }
+  }
+}
+
 int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* per_iolet_links,
-             int64_t* n_iolet_sites) {
+             int64_t* n_iolet_sites, std::vector<LinkRef>* links_out = nullptr) {
   if (!L || !o) return hlb_fail(HLB_ERR_ARG, "null lattice or options");
   if (L->n_sites < 1 || L->n_sites >= ((int64_t)1 << 31)) return hlb_fail(HLB_ERR_ARG, "n_sites must be in [1, 2^31)");
   if (!L->src || !L->xyz) return hlb_fail(HLB_ERR_ARG, "lattice needs xyz and src");
@@ -143,28 +180,28 @@ int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* p
     if (io.n_groups < 1) return hlb_fail(HLB_ERR_ARG, "iolet n_groups must be >= 1");
   }
   const int64_t n = L->n_sites;
-  per_iolet_links->assign((size_t)std::max(1, (int)L->n_iolets), 0);
-  std::vector<uint8_t> iolet_site((size_t)n, 0);
-  for (int i = 1; i < Q; ++i) {
-    const int32_t* row = L->src + (int64_t)(i - 1) * n;
-    for (int64_t x = 0; x < n; ++x) {
-      int32_t s = row[x];
-      if (s >= 0) {
-        if (s >= n) return hlb_fail(HLB_ERR_ARG, "src index out of range");
-      } else if (s <= -2) {
-        int k = -s - 2;
-        if (k >= L->n_iolets) return hlb_fail(HLB_ERR_ARG, "link code names a missing iolet");
-        if (L->iolets[k].kind == HLB_VELOCITY && L->amp_group) {
-          int g = L->amp_group[x];
-          if (g < 0 || g >= L->iolets[k].n_groups) return hlb_fail(HLB_ERR_ARG, "amplitude group out of range");
-        }
-        (*per_iolet_links)[k]++;
-        iolet_site[x] = 1;
-      }
-    }
+  // the 18 rows in parallel (one thread each); errors and links merged in row order
+  std::vector<RowCheck> rows(Q - 1);
+  {
+    std::vector<std::thread> pool;
+    pool.reserve(Q - 1);
+    for (int i = 1; i < Q; ++i) pool.emplace_back(check_row, L, i, &rows[(size_t)(i - 1)]);
+    for (auto& t : pool) t.join();
   }
+  per_iolet_links->assign((size_t)std::max(1, (int)L->n_iolets), 0);
+  for (const RowCheck& r : rows)
+    if (r.code != HLB_OK) return hlb_fail(r.code, r.msg);
+  std::vector<uint8_t> iolet_site((size_t)n, 0);
   *n_iolet_sites = 0;
-  for (int64_t x = 0; x < n; ++x) *n_iolet_sites += iolet_site[x];
+  for (const RowCheck& r : rows) {
+    for (size_t k = 0; k < r.per.size(); ++k) (*per_iolet_links)[k] += r.per[k];
+    for (const LinkRef& l : r.links)
+      if (!iolet_site[(size_t)l.x]) {
+        iolet_site[(size_t)l.x] = 1;
+        ++*n_iolet_sites;
+      }
+    if (links_out) links_out->insert(links_out->end(), r.links.begin(), r.links.end());
+  }
   return HLB_OK;
 }
 
@@ -222,7 +259,8 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   *out = nullptr;
   std::vector<int64_t> per;
   int64_t nis = 0;
-  int rc = validate(L, o, &per, &nis);
+  std::vector<LinkRef> links;
+  int rc = validate(L, o, &per, &nis, &links);
   if (rc) return rc;
   Layout y = layout(L, o, per, nis);
   if (!ws) return hlb_fail(HLB_ERR_WS, "null workspace");
@@ -288,19 +326,27 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->wk_on.assign((size_t)h->n_iolets, 0);
   h->n_iolet_sites = nis;
 
-  // link records sorted by (iolet, group, site, direction)
+  // link records sorted by (iolet, group, site, direction), from the links
+  // validate() collected (no further pass over the table)
   std::vector<int64_t> bucket_base(h->n_iolets + 1, 0);
   for (int k = 0; k < h->n_iolets; ++k)
     bucket_base[k + 1] = bucket_base[k] + (h->iolets[k].kind == HLB_VELOCITY ? h->iolets[k].n_groups : 1);
-  std::vector<int64_t> count(bucket_base[h->n_iolets] + 1, 0);
   auto group_of = [&](int k, int64_t x) -> int {
     return (h->iolets[k].kind == HLB_VELOCITY && L->amp_group) ? L->amp_group[x] : 0;
   };
-  for (int64_t x = 0; x < n; ++x)
-    for (int i = 1; i < Q; ++i) {
-      int32_t s = L->src[(int64_t)(i - 1) * n + x];
-      if (s <= -2) count[bucket_base[-s - 2] + group_of(-s - 2, x) + 1]++;
-    }
+  auto code_of = [&](const LinkRef& l) { return L->src[(int64_t)(l.dir - 1) * n + l.x]; };
+  auto bucket_of = [&](const LinkRef& l) {
+    const int k = -code_of(l) - 2;
+    return bucket_base[k] + group_of(k, l.x);
+  };
+  std::sort(links.begin(), links.end(), [&](const LinkRef& a, const LinkRef& b) {
+    const int64_t ba = bucket_of(a), bb = bucket_of(b);
+    if (ba != bb) return ba < bb;
+    if (a.x != b.x) return a.x < b.x;
+    return a.dir < b.dir;
+  });
+  std::vector<int64_t> count(bucket_base[h->n_iolets] + 1, 0);
+  for (const LinkRef& l : links) count[bucket_of(l) + 1]++;
   for (size_t b = 1; b < count.size(); ++b) count[b] += count[b - 1];
   h->n_links = y.n_links;
   h->link_begin.resize(h->n_iolets + 1);
@@ -315,18 +361,26 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   }
   std::vector<LinkRec> recs((size_t)std::max<int64_t>(y.n_links, 1));
   const int64_t sn = h->sn;
-  std::vector<int32_t> src((size_t)18 * sn, -1);  // padding entries are never gathered
-  for (int i = 0; i < 18; ++i) std::copy(L->src + (size_t)i * n, L->src + (size_t)(i + 1) * n, src.begin() + (size_t)i * sn);
-  std::vector<int64_t> fillpos(count.begin(), count.end() - 1);
-  for (int64_t x = 0; x < n; ++x)
-    for (int j = 1; j < Q; ++j) {
-      int32_t s = L->src[(int64_t)(j - 1) * n + x];
-      if (s > -2) continue;
-      const int k = -s - 2;
+  std::vector<int32_t> src((size_t)18 * sn);
+  {
+    // the caller's rows into the padded table, one thread per row; padding
+    // entries (never gathered) are -1
+    std::vector<std::thread> pool;
+    for (int i = 0; i < 18; ++i)
+      pool.emplace_back([&, i] {
+        std::copy(L->src + (size_t)i * n, L->src + (size_t)(i + 1) * n, src.begin() + (size_t)i * sn);
+        std::fill(src.begin() + (size_t)i * sn + n, src.begin() + (size_t)(i + 1) * sn, -1);
+      });
+    for (auto& t : pool) t.join();
+  }
+  for (int64_t r = 0; r < (int64_t)links.size(); ++r) {
+    const int64_t x = links[(size_t)r].x;
+    const int j = links[(size_t)r].dir;
+    {
+      const int k = -code_of(links[(size_t)r]) - 2;
       const hlb_iolet& io = h->iolets[k];
       const int gl = group_of(k, x);
-      const int64_t r = fillpos[bucket_base[k] + gl]++;
-      LinkRec& R = recs[r];
+      LinkRec& R = recs[(size_t)r];
       R.site = (int32_t)x;
       R.dir = (int8_t)j;
       R.kind = (int8_t)io.kind;
@@ -338,10 +392,10 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
         // Ladd weight at the link midpoint x - c_j / 2
         double m[3] = {L->xyz[3 * x] - 0.5 * cx(j), L->xyz[3 * x + 1] - 0.5 * cy(j), L->xyz[3 * x + 2] - 0.5 * cz(j)};
         double v[3] = {m[0] - io.centre[0], m[1] - io.centre[1], m[2] - io.centre[2]};
-        double sn = v[0] * io.normal[0] + v[1] * io.normal[1] + v[2] * io.normal[2];
+        double an = v[0] * io.normal[0] + v[1] * io.normal[1] + v[2] * io.normal[2];  // axial coordinate
         double r2 = 0;
         for (int a = 0; a < 3; ++a) {
-          double w = v[a] - sn * io.normal[a];
+          double w = v[a] - an * io.normal[a];
           r2 += w * w;
         }
         double W = std::max(0.0, 1.0 - r2 / (io.radius * io.radius));
@@ -351,19 +405,17 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
       }
       src[(size_t)(j - 1) * sn + x] = -(int32_t)(2 + r);
     }
+  }
 
   cudaStream_t st = h->stream;
   int64_t nb = hlb_reduce_partials(n);
   std::vector<int64_t> begin(h->link_begin);
   std::vector<double> ampf(std::max(g, 1), 0.0);
   std::vector<int32_t> isites;
-  isites.reserve((size_t)nis);
-  for (int64_t x = 0; x < n; ++x)
-    for (int i = 1; i < Q; ++i)
-      if (L->src[(int64_t)(i - 1) * n + x] <= -2) {
-        isites.push_back((int32_t)x);
-        break;
-      }
+  isites.reserve(links.size());
+  for (const LinkRef& l : links) isites.push_back(l.x);
+  std::sort(isites.begin(), isites.end());
+  isites.erase(std::unique(isites.begin(), isites.end()), isites.end());
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && y.n_links > 0)
