@@ -86,8 +86,10 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // 19 gathered values of mu(t+1) can reuse the registers.  Then
 // lam = G_t^T mu(t+1) and mu_j(t) = (1 - omega) lam_j + omega (S0 + (c_j - u).B)
 // plus the probe term.  The index row is read twice (once per gather); the
-// second read hits L1.  A TMA-staged index tile (as in k_step) measured no
-// faster here and costs 56 KiB of shared memory per block.
+// second read hits L1.  Staging the index rows in shared memory with bulk
+// copies measured no faster here and costs 56 KiB of shared memory per
+// block; issuing both gathers together (no parked parts, 3 or 2 blocks per
+// SM) measured slower.
 template <typename S, bool GPREV, bool WIDE>
 __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const S* __restrict__ mu_next,
                                                S* __restrict__ mu_out, const int32_t* __restrict__ src,
@@ -110,7 +112,7 @@ __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const
                                   : slot<WIDE>(i, n, xi)));
       iolet |= s <= -2;
     }
-    if (!iolet) {  // iolet sites: k_adjoint_iolet
+    if (!iolet) {  // iolet sites: adjoint_iolet_site
       m = moments<R>(h);
       const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
 #pragma unroll
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2
     d = adjoint_iolet_site<S, GPREV>(prev, cur, mu_next, mu_out, src, links, amp, ap, pm, sites, nsites, dlink,
                                      store, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
   } else {
-    const unsigned k = b - min(n_iolet_blocks, j + 1);  // bulk tile: blocks before b that are not iolet blocks
+    const unsigned k = b - min(n_iolet_blocks, j + 1);  // bulk block: blocks before b that are not iolet blocks
     d = adjoint_site<S, GPREV, WIDE>(prev, mu_next, mu_out, src, ap, pm, store, (int64_t)k * BLOCK + threadIdx.x, neq);
   }
   const double bs = block_sum(d, sh);

@@ -316,7 +316,7 @@ def _one_step_within_rounding(lat, tau, bc, prec, scheme, w, warm=5, wide=False,
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_16bit_one_step_within_storage_rounding(d3q19, prec, scheme, wide):
-    """Ragged several-tile tree (pulsatile inlet, 7 pressure outlets)."""
+    """Ragged tree of many 256-site blocks (pulsatile inlet, 4 pressure outlets)."""
     _, w = d3q19
     lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0)
     assert lat.n % 256
