@@ -108,7 +108,8 @@ typedef struct {
 /* precision: HLB_FP32 / HLB_BF16 / HLB_FP16 / HLB_FP64 storage.
  * scheme: HLB_PULL_AB (two population buffers, pull gather) or HLB_AA
  *   (one buffer, alternating in-place even/odd steps); AUTO picks the
- *   faster measured scheme.
+ *   scheme measured faster for the lattice size: pull A-B below 4M sites
+ *   (one launch per step), AA from 4M sites on (fewer bytes per site).
  * ladd_rho_one: 1 = use rho = 1 in the Ladd correction instead of the
  *   site's density (the paper does not say which density).
  * ghost_full_u: 1 = pressure-iolet ghost velocity u instead of (u.n) n.

@@ -205,9 +205,17 @@ int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* p
   return HLB_OK;
 }
 
-// AUTO resolves to the scheme measured faster on GB300: the AA pattern moves
-// 188 B per FP32 site update against 224 B for pull A-B.
-int32_t resolve_scheme(int32_t scheme) { return scheme == HLB_SCHEME_AUTO ? HLB_AA : scheme; }
+// AUTO resolves to the scheme measured faster on GB300 for the lattice size.
+// The AA pattern moves 188 B per FP32 site update against 224 B for pull
+// A-B, but needs a second launch per step for its iolet-site pass (about
+// 20 us of latency-bound work whatever the size).  Per step, AA took 28 ps
+// per site + ~21 us and A-B 34 ps per site + ~2 us, so AA wins above about
+// 3.2M sites: 2.0M sites 79 vs 77 us, 20M sites 585 vs 682 us.
+constexpr int64_t AA_MIN_SITES = 4000000;
+int32_t resolve_scheme(int32_t scheme, int64_t n) {
+  if (scheme != HLB_SCHEME_AUTO) return scheme;
+  return n >= AA_MIN_SITES ? HLB_AA : HLB_PULL_AB;
+}
 
 Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int64_t>& per_iolet,
               int64_t n_iolet_sites) {
@@ -220,7 +228,7 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
     if (L->iolets[k].kind == HLB_VELOCITY) y.n_groups += L->iolets[k].n_groups;
   size_t off = 0;
   y.f0 = off; off += state;
-  y.f1 = off; off += resolve_scheme(o->scheme) == HLB_AA ? 0 : state;
+  y.f1 = off; off += resolve_scheme(o->scheme, n) == HLB_AA ? 0 : state;
   y.src = off; off += align_up(sizeof(int32_t) * 18 * (size_t)row_stride(n));
   y.links = off; off += align_up(sizeof(LinkRec) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.amp = off; off += align_up(sizeof(double) * (size_t)std::max(y.n_groups, 1));
@@ -281,7 +289,7 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   h->n_iolets = L->n_iolets;
   h->iolets.assign(L->iolets, L->iolets + L->n_iolets);
   h->precision = o->precision;
-  h->scheme = resolve_scheme(o->scheme);
+  h->scheme = resolve_scheme(o->scheme, n);
   h->ladd_rho_one = o->ladd_rho_one ? 1 : 0;
   h->ghost_full_u = o->ghost_full_u ? 1 : 0;
   h->off32 = !o->wide_offsets && (uint64_t)Q * (uint64_t)h->sn <= 0xffffffffull;

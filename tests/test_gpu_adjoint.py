@@ -26,8 +26,10 @@ def _setup(x, lat, amps):
     x.init_equilibrium()
 
 
-@pytest.mark.parametrize("opts,wide", [((False, False), False), ((True, True), False), ((False, False), True)])
-def test_fp64_adjoint_equals_oracle(opts, wide):
+@pytest.mark.parametrize("opts,wide,scheme", [((False, False), False, "ab"), ((True, True), False, "aa"),
+                                             ((False, False), True, "aa"), ((True, True), True, "ab")])
+def test_fp64_adjoint_equals_oracle(opts, wide, scheme):
+    """The solver's own scheme only decides how the final state is handed back."""
     lat = geo.tree(1, 7, root_radius=4.0, length_ratio=5.0, n_sectors=2, n_rings=2)
     N, tau = 40, 0.7
     probe = np.nonzero(lat.xyz[:, 2] == int(lat.info["root_length"] // 2))[0]
@@ -38,7 +40,7 @@ def test_fp64_adjoint_equals_oracle(opts, wide):
     _setup(o, lat, amps)
     J_o, dtau_o, damp_o = o.adjoint(N, probe, target, [0, 0, 1])
     s = hemegb.Solver(lat, tau=tau, precision="fp64", ladd_rho_one=opts[0], ghost_full_u=opts[1],
-                      wide_offsets=wide)
+                      wide_offsets=wide, scheme=scheme)
     _setup(s, lat, amps)
     J, dtau, damp = s.adjoint(N, probe, target, [0, 0, 1])
     assert s.t == N
