@@ -162,13 +162,13 @@ def aggregate_ranks(ms_local, updates_local, dist=None, device="cpu"):
     return float(t.item()), float(u.item())
 
 
-def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55):
+def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55, wide=False):
     """Time `steps` launches with a CUDA event after each (solver stream).
 
     Returns (total_ms, per-step durations in ms, solver time before the
     first timed step)."""
     from paper_2202_11770_gb300 import hemegb
-    s = hemegb.Solver(lat, tau=tau, precision=precision, scheme=scheme)
+    s = hemegb.Solver(lat, tau=tau, precision=precision, scheme=scheme, wide_offsets=wide)
     set_bc(s, lat)
     s.init_equilibrium()
     s.step(warmup)
@@ -406,7 +406,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     prec0 = args.precision if args.quick else "fp32"
-    ms, durs, t_first = time_form(lat, prec0, scheme, args.steps, args.warmup, torch, dist, tau=args.tau)
+    ms, durs, t_first = time_form(lat, prec0, scheme, args.steps, args.warmup, torch, dist, tau=args.tau,
+                                  wide=args.wide_offsets)
     clk = clocks.stop()
     ms, total_updates = aggregate_ranks(ms, n * args.steps, dist, "cuda")
     value = total_updates / (ms * 1e-3) / 1e6
@@ -491,6 +492,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="one form only, no e2e (profiling runs)")
     ap.add_argument("--tau", type=float, default=0.55, help="relaxation time of the timed headline form")
+    ap.add_argument("--wide-offsets", action="store_true",
+                    help="time the large-lattice (direction-pair offset) kernels at this size")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"],
                     help="storage precision of the one form timed by --quick")
     ap.add_argument("--scheme", default="aa", choices=["ab", "aa"],

