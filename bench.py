@@ -67,10 +67,10 @@ ELEM = {"fp32": 4, "bf16": 2, "fp16": 2, "fp64": 8}
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": "dd8b947313717769",
+TRAFFIC = {"sha": "7adcbba9671fe08a",
            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site tree
-           "bytes_per_site": {"k_aa_odd": (2960249600 + 1488131072) / 20000864,
-                              "k_step": (3050591744 + 1482896640) / 20000864}}
+           "bytes_per_site": {"k_aa_odd": (2960304128 + 1488711424) / 20000864,
+                              "k_step": (3050549504 + 1482938624) / 20000864}}
 
 
 def kernel_sha() -> str:
