@@ -635,8 +635,8 @@ extern "C" int hlb_adjoint_workspace_bytes(const hlb_solver* h, int64_t nsteps, 
   return HLB_OK;
 }
 
-extern "C" int hlb_adjoint_run(hlb_solver* h, int64_t nsteps, const hlb_objective* obj, void* ws, size_t ws_bytes,
-                               double* J, double* dtau, double* damp) {
+static int adjoint_run_impl(hlb_solver* h, int64_t nsteps, const hlb_objective* obj, void* ws, size_t ws_bytes,
+                            double* J, double* dtau, double* damp) {
   int rc = check_objective(h, nsteps, obj);
   if (rc) return rc;
   if (h->any_wk()) return hlb_fail(HLB_ERR_ARG, "the adjoint does not differentiate Windkessel outlets");
@@ -646,4 +646,9 @@ extern "C" int hlb_adjoint_run(hlb_solver* h, int64_t nsteps, const hlb_objectiv
     return hlb_fail(HLB_ERR_WS, "adjoint workspace too small: need " + std::to_string(y.total) + " bytes");
   if (h->precision == HLB_FP64) return run_adjoint<double>(h, nsteps, obj, (char*)ws, y, J, dtau, damp);
   return run_adjoint<float>(h, nsteps, obj, (char*)ws, y, J, dtau, damp);
+}
+
+extern "C" int hlb_adjoint_run(hlb_solver* h, int64_t nsteps, const hlb_objective* obj, void* ws, size_t ws_bytes,
+                               double* J, double* dtau, double* damp) {
+  return hlb_no_throw([&] { return adjoint_run_impl(h, nsteps, obj, ws, ws_bytes, J, dtau, damp); });
 }

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <memory>
 #include <new>
 #include <string>
 #include <thread>
@@ -251,7 +252,7 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
 
 }  // namespace
 
-extern "C" int hlb_workspace_bytes(const hlb_lattice* L, const hlb_options* o, size_t* bytes) {
+static int workspace_bytes_impl(const hlb_lattice* L, const hlb_options* o, size_t* bytes) {
   if (!bytes) return hlb_fail(HLB_ERR_ARG, "null output");
   std::vector<int64_t> per;
   int64_t nis = 0;
@@ -261,8 +262,12 @@ extern "C" int hlb_workspace_bytes(const hlb_lattice* L, const hlb_options* o, s
   return HLB_OK;
 }
 
-extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, size_t ws_bytes, hlb_stream stream,
-                          hlb_solver** out) {
+extern "C" int hlb_workspace_bytes(const hlb_lattice* L, const hlb_options* o, size_t* bytes) {
+  return hlb_no_throw([&] { return workspace_bytes_impl(L, o, bytes); });
+}
+
+static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, size_t ws_bytes, hlb_stream stream,
+                       hlb_solver** out, std::unique_ptr<hlb_solver>* owner) {
   if (!out) return hlb_fail(HLB_ERR_ARG, "null output");
   *out = nullptr;
   std::vector<int64_t> per;
@@ -281,8 +286,8 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
     return hlb_fail(HLB_ERR_WS, "workspace is not device memory");
   }
 
-  hlb_solver* h = new (std::nothrow) hlb_solver();
-  if (!h) return hlb_fail(HLB_ERR_NOMEM, "host allocation failed");
+  owner->reset(new hlb_solver());
+  hlb_solver* h = owner->get();
   const int64_t n = L->n_sites;
   h->n = n;
   h->sn = row_stride(n);
@@ -466,15 +471,18 @@ extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_lflux, 0, sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->state_bytes(), st);  // rest: h = f - w = 0
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) {
-    delete h;
-    return hlb_cuda_fail(e, "hlb_create upload");
-  }
+  if (e != cudaSuccess) return hlb_cuda_fail(e, "hlb_create upload");  // the owner frees h
   h->cur = 0;
   h->phase = 0;
   h->t = 0;
-  *out = h;
+  *out = owner->release();
   return HLB_OK;
+}
+
+extern "C" int hlb_create(const hlb_lattice* L, const hlb_options* o, void* ws, size_t ws_bytes, hlb_stream stream,
+                          hlb_solver** out) {
+  std::unique_ptr<hlb_solver> owner;
+  return hlb_no_throw([&] { return create_impl(L, o, ws, ws_bytes, stream, out, &owner); });
 }
 
 extern "C" int hlb_destroy(hlb_solver* h) {
@@ -498,7 +506,7 @@ extern "C" int hlb_set_tau(hlb_solver* h, double tau) {
   return HLB_OK;
 }
 
-extern "C" int hlb_set_velocity_waveform(hlb_solver* h, int32_t k, const double* amp, int32_t n_groups,
+static int hlb_set_velocity_waveform_impl(hlb_solver* h, int32_t k, const double* amp, int32_t n_groups,
                                          const hlb_waveform* w) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
   if (k < 0 || k >= h->n_iolets || h->iolets[k].kind != HLB_VELOCITY)
@@ -517,7 +525,12 @@ extern "C" int hlb_set_velocity_waveform(hlb_solver* h, int32_t k, const double*
   return HLB_OK;
 }
 
-extern "C" int hlb_set_pressure(hlb_solver* h, int32_t k, const hlb_waveform* w) {
+extern "C" int hlb_set_velocity_waveform(hlb_solver* h, int32_t k, const double* amp, int32_t n_groups,
+                                         const hlb_waveform* w) {
+  return hlb_no_throw([&] { return hlb_set_velocity_waveform_impl(h, k, amp, n_groups, w); });
+}
+
+static int hlb_set_pressure_impl(hlb_solver* h, int32_t k, const hlb_waveform* w) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
   if (k < 0 || k >= h->n_iolets || h->iolets[k].kind != HLB_PRESSURE)
     return hlb_fail(HLB_ERR_ARG, "not a pressure iolet");
@@ -527,6 +540,10 @@ extern "C" int hlb_set_pressure(hlb_solver* h, int32_t k, const hlb_waveform* w)
   h->wave[k] = hw;
   h->wk_on[k] = 0;
   return HLB_OK;
+}
+
+extern "C" int hlb_set_pressure(hlb_solver* h, int32_t k, const hlb_waveform* w) {
+  return hlb_no_throw([&] { return hlb_set_pressure_impl(h, k, w); });
 }
 
 extern "C" int hlb_set_windkessel(hlb_solver* h, int32_t k, double Rp, double C, double Rd, double rho_d,
@@ -632,7 +649,7 @@ extern "C" int hlb_read_macros(hlb_solver* h, float* rho, float* u, float* wss, 
   return HLB_OK;
 }
 
-extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
+static int hlb_reduce_impl(hlb_solver* h, double* mass, double* flux) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
   const int64_t nb = hlb_reduce_partials(h->n);
   double* out = h->d_red + nb + (h->n_iolets + 1);
@@ -647,7 +664,11 @@ extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
   return HLB_OK;
 }
 
-extern "C" int hlb_iolet_monitor(hlb_solver* h, double* flux, double* u_max, double* rho_mean) {
+extern "C" int hlb_reduce(hlb_solver* h, double* mass, double* flux) {
+  return hlb_no_throw([&] { return hlb_reduce_impl(h, mass, flux); });
+}
+
+static int hlb_iolet_monitor_impl(hlb_solver* h, double* flux, double* u_max, double* rho_mean) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
   const int K = h->n_iolets;
   if (K == 0) return HLB_OK;
@@ -667,6 +688,10 @@ extern "C" int hlb_iolet_monitor(hlb_solver* h, double* flux, double* u_max, dou
     if (rho_mean) rho_mean[k] = host[(size_t)(K + k)];
   }
   return HLB_OK;
+}
+
+extern "C" int hlb_iolet_monitor(hlb_solver* h, double* flux, double* u_max, double* rho_mean) {
+  return hlb_no_throw([&] { return hlb_iolet_monitor_impl(h, flux, u_max, rho_mean); });
 }
 
 extern "C" int hlb_get_state(hlb_solver* h, void* f, int32_t where, int64_t* t) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -89,8 +91,21 @@ struct hlb_solver {
 
 // thread-local error text
 int hlb_fail(int code, const std::string& msg);
-// HLB_OK, or HLB_ERR_CUDA if a kernel recorded a timed-out wait (synchronises).
+// HLB_ERR_CUDA with the runtime's message for e (and where it happened).
 int hlb_cuda_fail(cudaError_t e, const char* where);
+
+// Runs an entry point's body; host allocation or thread failures become
+// HLB_ERR_NOMEM instead of exceptions crossing the C ABI.
+template <typename F>
+int hlb_no_throw(F f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return hlb_fail(HLB_ERR_NOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return hlb_fail(HLB_ERR_NOMEM, std::string("host resource failure: ") + e.what());
+  }
+}
 
 // ---- launchers (hlb_forward.cu) ----
 // One pull A-B time step from fin into fout (gather: fin holds s'(t-1)).
