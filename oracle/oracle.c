@@ -37,6 +37,11 @@
  *   - Adjoint: the exact transpose of the linearised step above, by explicit
  *     per-site 19x19 Jacobians, for an objective averaging squared deviations
  *     of the axial velocity at probe sites from a target.
+ *   - Iolet waveforms: constant, cosine, or a table of samples evenly spaced
+ *     over one period, interpolated linearly and periodically (the paper's
+ *     Section 6 drives its pipe with such a measured one-beat profile).
+ *   - Windkessel outlets (not the paper's method; its Section 7 names outlet
+ *     resistance models as future work): see wk_t.
  */
 #include <math.h>
 #include <stdint.h>
