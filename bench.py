@@ -47,22 +47,29 @@ def workload_name(n, tau):
     return (f"seeded depth-6 vessel tree, {n / 1e6:.0f}M fluid sites, D3Q19 LBGK tau={tau:g}, "
             "pulsatile Ladd inlet, 64 pressure outlets")
 
+# Index bytes per site: the int32 streaming-index table (18 x 4 B), or its
+# compact form (18 x 2 B of offsets plus 20 int32 tile bases per 256 sites).
+INDEX_BYTES = {False: 18 * 4, True: 18 * 2 + 20 * 4 / 256}
+
+
 # Algorithmic bytes per site update (storage element size e): 19 populations
-# read + 19 written, plus the int32 streaming-index table (18 x 4 B) when the
-# kernel gathers through it.  Pull A-B gathers every step; the AA pattern
-# only on odd steps.  Boundary-link records are O(boundary sites), not counted.
-def bytes_per_site(elem: int, kernel: str = "ab") -> float:
+# read + 19 written, plus the index table when the kernel gathers through
+# it.  Pull A-B gathers every step; the AA pattern only on odd steps.
+# Boundary-link records are O(boundary sites), not counted.
+def bytes_per_site(elem: int, kernel: str = "ab", compact: bool = False) -> float:
     local = 19 * elem * 2
+    idx = INDEX_BYTES[bool(compact)]
     if kernel in ("ab", "aa_odd"):
-        return local + 18 * 4
+        return local + idx
     if kernel == "aa_even":
         return local
     if kernel == "aa":
-        return local + 18 * 4 / 2
+        return local + idx / 2
     raise ValueError(kernel)
 
 
 ELEM = {"fp32": 4, "bf16": 2, "fp16": 2, "fp64": 8}
+CTYPE = {"fp32": "float", "bf16": "__nv_bfloat16", "fp16": "__half", "fp64": "double"}
 
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
@@ -162,13 +169,14 @@ def aggregate_ranks(ms_local, updates_local, dist=None, device="cpu"):
     return float(t.item()), float(u.item())
 
 
-def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55, wide=False):
+def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55, wide=False, full_index=False):
     """Time `steps` launches with a CUDA event after each (solver stream).
 
     Returns (total_ms, per-step durations in ms, solver time before the
-    first timed step)."""
+    first timed step, whether the kernels read the compact index table)."""
     from paper_2202_11770_gb300 import hemegb
-    s = hemegb.Solver(lat, tau=tau, precision=precision, scheme=scheme, wide_offsets=wide)
+    s = hemegb.Solver(lat, tau=tau, precision=precision, scheme=scheme, wide_offsets=wide, full_index=full_index)
+    compact = s.compact_index
     set_bc(s, lat)
     s.init_equilibrium()
     s.step(warmup)
@@ -189,7 +197,7 @@ def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55,
     assert math.isfinite(mass)
     del s
     torch.cuda.empty_cache()
-    return total, durs, t_first
+    return total, durs, t_first, compact
 
 
 def kernel_names(n):
@@ -197,15 +205,16 @@ def kernel_names(n):
     return ("k_step", "k_aa_odd")
 
 
-def form_stats(lat, precision, scheme, total, durs, t_first, steps, peak):
+def form_stats(lat, precision, scheme, total, durs, t_first, steps, peak, compact):
     """MLUPS, algorithmic GB/s and per-kernel rooflines of one timed form
     (CUDA events around every step: each step is one kernel launch)."""
     n = lat.n
     k_ab, k_odd = kernel_names(n)
     e = ELEM[precision]
-    out = {"scheme": scheme, "mlups": n * steps / (total * 1e-3) / 1e6, "ms_per_step": total / steps}
+    out = {"scheme": scheme, "mlups": n * steps / (total * 1e-3) / 1e6, "ms_per_step": total / steps,
+           "index": "compact" if compact else "int32"}
     if scheme == "ab":
-        b = bytes_per_site(e, "ab")
+        b = bytes_per_site(e, "ab", compact)
         gbs = b * n / (total / steps * 1e-3) / 1e9
         out.update(gbs=gbs, frac_of_measured_peak=gbs / peak, bytes_per_site=b,
                    kernels={k_ab: {"launches": steps, "mean_us": total / steps * 1e3, "gbs": gbs,
@@ -213,10 +222,10 @@ def form_stats(lat, precision, scheme, total, durs, t_first, steps, peak):
     else:
         odd = [d for k, d in enumerate(durs) if (t_first + k) % 2 == 1]
         even = [d for k, d in enumerate(durs) if (t_first + k) % 2 == 0]
-        b = bytes_per_site(e, "aa")
+        b = bytes_per_site(e, "aa", compact)
         gbs = b * n / (total / steps * 1e-3) / 1e9
         kern = {}
-        for name, ds, kb in ((k_odd, odd, bytes_per_site(e, "aa_odd")),
+        for name, ds, kb in ((k_odd, odd, bytes_per_site(e, "aa_odd", compact)),
                              ("k_aa_even", even, bytes_per_site(e, "aa_even"))):
             m = sum(ds) / len(ds)
             g = kb * n / (m * 1e-3) / 1e9
@@ -262,7 +271,7 @@ def e2e_job(lat, steps, torch):
     return n * steps / dt / 1e6, h2d_step, d2h_step, t_create, dt
 
 
-def adjoint_ratio(steps, torch, sites=2_000_000):
+def adjoint_ratio(steps, torch, sites=2_000_000, full_index=False):
     """Adjoint (forward with sqrt(N) checkpoints + recompute + reverse) vs
     forward-only time over the same N steps: seeded depth-4 tree, ~2M sites,
     64 inlet amplitude groups, FP32."""
@@ -270,7 +279,7 @@ def adjoint_ratio(steps, torch, sites=2_000_000):
     lat, obj = workloads.adjoint_case(target_sites=sites)
     fwd = {}
     for sch in ("ab", "aa"):
-        s = hemegb.Solver(lat, tau=0.55, precision="fp32", scheme=sch)
+        s = hemegb.Solver(lat, tau=0.55, precision="fp32", scheme=sch, full_index=full_index)
         workloads.apply_tree_bc(s, lat)
         s.init_equilibrium()
         s.step(10)
@@ -283,7 +292,7 @@ def adjoint_ratio(steps, torch, sites=2_000_000):
         torch.cuda.synchronize()
         fwd[sch] = e0.elapsed_time(e1)
         del s
-    s = hemegb.Solver(lat, tau=0.55, precision="fp32", scheme="auto")
+    s = hemegb.Solver(lat, tau=0.55, precision="fp32", scheme="auto", full_index=full_index)
     workloads.apply_tree_bc(s, lat)
     ws = s.adjoint_workspace(steps, obj.sites.size)
     s.init_equilibrium()
@@ -302,7 +311,7 @@ def adjoint_ratio(steps, torch, sites=2_000_000):
            "checkpoint_interval": K, "forward_ms": fwd, "adjoint_ms": adj,
            "ratio": adj / min(fwd.values()), "ratio_vs_pull_ab": adj / fwd["ab"],
            "J": J, "dJ_dtau": dtau, "probe_sites": int(obj.sites.size),
-           "adjoint_workspace_gb": ws[2] / 1e9}
+           "adjoint_workspace_gb": ws[2] / 1e9, "index": "compact" if s.compact_index else "int32"}
     del s, ws
     torch.cuda.empty_cache()
     return out
@@ -406,16 +415,16 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     prec0 = args.precision if args.quick else "fp32"
-    ms, durs, t_first = time_form(lat, prec0, scheme, args.steps, args.warmup, torch, dist, tau=args.tau,
-                                  wide=args.wide_offsets)
+    ms, durs, t_first, compact = time_form(lat, prec0, scheme, args.steps, args.warmup, torch, dist, tau=args.tau,
+                                           wide=args.wide_offsets, full_index=args.full_index)
     clk = clocks.stop()
     ms, total_updates = aggregate_ranks(ms, n * args.steps, dist, "cuda")
     value = total_updates / (ms * 1e-3) / 1e6
-    head = form_stats(lat, prec0, scheme, ms, durs, t_first, args.steps, peak)
+    head = form_stats(lat, prec0, scheme, ms, durs, t_first, args.steps, peak, compact)
     kname = kernel_names(n)[0 if scheme == "ab" else 1]
     kst = head["kernels"][kname]
     traffic = None
-    if TRAFFIC["sha"] == kernel_sha() and kname in TRAFFIC["bytes_per_site"]:
+    if TRAFFIC["sha"] == kernel_sha() and compact and kname in TRAFFIC["bytes_per_site"]:
         traffic = TRAFFIC["bytes_per_site"][kname] * n
 
     forms = {f"{prec0}_{scheme}": head}
@@ -424,12 +433,13 @@ def run_ours(args):
             for sch in ("ab", "aa"):
                 if f"{prec}_{sch}" in forms:
                     continue
-                tot, d, tf = time_form(lat, prec, sch, args.steps, args.warmup, torch, dist)
-                forms[f"{prec}_{sch}"] = form_stats(lat, prec, sch, tot, d, tf, args.steps, peak)
+                tot, d, tf, ct = time_form(lat, prec, sch, args.steps, args.warmup, torch, dist,
+                                           full_index=args.full_index)
+                forms[f"{prec}_{sch}"] = form_stats(lat, prec, sch, tot, d, tf, args.steps, peak, ct)
 
     adjoint = None
     if not args.quick and args.adjoint_steps > 0:
-        adjoint = adjoint_ratio(args.adjoint_steps, torch)
+        adjoint = adjoint_ratio(args.adjoint_steps, torch, full_index=args.full_index)
 
     e2e = None
     if not args.quick:
@@ -451,11 +461,12 @@ def run_ours(args):
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16 storage, f32 math", "fp16": "f16 storage, f32 math", "fp64": "f64"}[prec0], "data": "synthetic",
             "config": {"workload": workload_name(n, args.tau), "n_sites": n, "tau": args.tau,
                        "scheme": {"ab": "pull A-B", "aa": "AA pattern"}[scheme],
+                       "index": ("compact: 16-bit offsets from per-tile bases" if compact else "int32 table"),
                        "parallelism": f"replicas x{world}", "l2": f"working set {n * head['bytes_per_site'] / 1e9:.1f} GB/step >> 129 MB L2, no flush",
                        "fill": round(lat.info["fill"], 4)},
             "roofline": {"bound": "hbm", "achieved": kst["gbs"], "peak": peak, "unit": "GB/s",
                          "frac": kst["gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": kname + "<float>", "launches": kst["launches"], "mean_us": kst["mean_us"],
+                         "kernel": f"{kname}<{CTYPE[prec0]}>", "launches": kst["launches"], "mean_us": kst["mean_us"],
                          "timed": "CUDA events around each step" + (
                              " (odd step = k_aa_odd + the k_aa_fix pass)" if scheme == "aa" else ""),
                          "algorithmic_bytes_per_site": kst["bytes_per_site"],
@@ -492,6 +503,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="one form only, no e2e (profiling runs)")
     ap.add_argument("--tau", type=float, default=0.55, help="relaxation time of the timed headline form")
+    ap.add_argument("--full-index", action="store_true",
+                    help="time the kernels on the int32 index table instead of its compact form")
     ap.add_argument("--wide-offsets", action="store_true",
                     help="time the large-lattice (direction-pair offset) kernels at this size")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"],
@@ -514,7 +527,8 @@ def main():
     elif args.adjoint_only:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps({"adjoint": adjoint_ratio(args.adjoint_steps, torch, args.adjoint_sites)}))
+        print(json.dumps({"adjoint": adjoint_ratio(args.adjoint_steps, torch, args.adjoint_sites,
+                                                   full_index=args.full_index)}))
     else:
         run_ours(args)
 

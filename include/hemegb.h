@@ -119,13 +119,22 @@ typedef struct {
  *   226M sites), and from the start of the direction pair (rows 2p-1, 2p)
  *   above that, which covers any lattice below 2^31 sites.  This flag selects
  *   the second form at any size, so that it can be checked on small
- *   lattices.  Results are identical either way. */
+ *   lattices.  Results are identical either way.
+ * full_index: 1 = the step and adjoint kernels read the 32-bit streaming
+ *   index table.  By default (0) they read a compact copy built at create:
+ *   per 256-site tile and direction the smallest fluid source, and per site
+ *   and direction a 16-bit offset from it (36 instead of 72 bytes a site).
+ *   The lattice's sources are ordered as its sites, so in a vessel lattice
+ *   the sources of one direction over a tile span a few hundred sites; if
+ *   some tile's span does not fit 16 bits the library uses the 32-bit table
+ *   (hlb_compact_index reports which).  Results are identical either way. */
 typedef struct {
   int32_t precision;
   int32_t scheme;
   int32_t ladd_rho_one;
   int32_t ghost_full_u;
   int32_t wide_offsets;
+  int32_t full_index;
 } hlb_options;
 
 /* Time-dependent scalar w(t):
@@ -168,6 +177,9 @@ int hlb_create(const hlb_lattice* lat, const hlb_options* opt, void* dev_ws, siz
 int hlb_destroy(hlb_solver* h);
 int hlb_set_stream(hlb_solver* h, hlb_stream stream);
 int64_t hlb_n_sites(const hlb_solver* h);
+/* 1 if the step and adjoint kernels read the compact index table, 0 if the
+ * 32-bit one (see hlb_options.full_index); HLB_ERR_ARG for a null handle. */
+int hlb_compact_index(const hlb_solver* h);
 
 /* Relaxation time tau (Eq. 3a, Delta t = 1); viscosity nu = (tau - 1/2)/3
  * (Eq. 8).  HLB_ERR_ARG unless tau > 1/2. */
@@ -254,8 +266,9 @@ int hlb_set_state(hlb_solver* h, const void* f, int32_t where, int64_t t);
  * transpose of every step (collision, streaming, bounce-back, Ladd and
  * pressure boundaries), recomputing states from sqrt(N)-spaced checkpoints.
  * Outputs J, dJ/dtau and dJ/da_g for every amplitude group of every velocity
- * iolet (iolet order, then group).  The state is left at t + N.  FP32 and
- * FP64 storage only.  hlb_adjoint_workspace_bytes gives the device workspace
+ * iolet (iolet order, then group).  The forward sweep runs the solver's own
+ * scheme; the state is left at t + N as that scheme's step leaves it.  FP32
+ * and FP64 storage only.  hlb_adjoint_workspace_bytes gives the device workspace
  * (checkpoints + one segment of states + adjoint buffers). */
 int hlb_adjoint_workspace_bytes(const hlb_solver* h, int64_t nsteps, int64_t n_probe,
                                 size_t* bytes);

@@ -17,7 +17,10 @@
 // opp(i).  One kernel per reverse step reads the index table and gathers
 // both mu(t+1) and s'(t-1) (to recompute f(t)).  J itself is summed in the
 // reverse sweep too, where f(t)'s moments are at hand, so the forward sweep
-// runs the plain step kernels and nothing else.
+// runs the plain step kernels of the solver's scheme and nothing else.  The
+// reverse kernel reads the int32 index table: with the compact table (whose
+// decoding needs more registers) it spilled at four blocks per SM and
+// measured slower.
 #include <math.h>
 
 #include <algorithm>
@@ -458,7 +461,7 @@ size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 AdjLayout adj_layout(const hlb_solver* h, int64_t N, int64_t np) {
   AdjLayout y;
-  // checkpoints are taken after odd AA steps, so the interval is even
+  // AA checkpoints are taken after odd steps, so the interval is even
   y.K = (int64_t)ceil(sqrt((double)N));
   if (y.K < 2) y.K = 2;
   if (y.K & 1) ++y.K;
@@ -543,27 +546,42 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   TRY(cudaMemcpyAsync(gbegin, h->group_link_begin.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, st));
   Probe pr{d_sites, d_target, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N, np};
 
-  // ---- forward with the AA kernels on one working buffer; checkpoint c is
-  // the pre-collision state f(cK), taken after an odd step (natural layout) ----
+  // ---- forward sweep in the solver's own scheme (the faster one for the
+  // lattice size when it was created with AUTO).  Checkpoint 0 is f(t0) in
+  // natural layout; checkpoint c >= 1 is, for AA, f(cK) taken after an odd
+  // step (natural layout) and, for pull A-B, s'(cK - 1), from which the
+  // segment's first step gathers f(cK). ----
   const int64_t K = y.K, nck = y.nck;
-  void* W = sg(0);
-  TRY(cudaMemcpyAsync(W, ck(0), h->state_bytes(), cudaMemcpyDeviceToDevice, st));
-  bool swapped = false;
-  for (int64_t s = 0; s < N; ++s) {
-    TRY(hlb_launch_aa(h, W, swapped, t0 + s, st));
-    swapped = !swapped;
-    if (!swapped && (s + 1) % K == 0 && (s + 1) / K < nck)
-      TRY(cudaMemcpyAsync(ck((s + 1) / K), W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
-  }
-  // The final state f(t0 + N) goes straight into the solver's own buffer,
-  // which is free during the run (the start state was copied to checkpoint
-  // 0): AA keeps its layout, pull A-B receives the pre-collision form.
-  int fin_mode = swapped ? HLB_READ_GATHER_AA : HLB_READ_LOCAL;
-  if (h->scheme == HLB_AA || !swapped) {
-    TRY(cudaMemcpyAsync(h->f[0], W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+  const bool ab = h->scheme == HLB_PULL_AB;
+  int fin_mode;
+  if (ab) {
+    // two working buffers (segment slots 0 and 1); the final s'(t0 + N - 1)
+    // goes straight into the solver's buffer 0, which is free during the
+    // run (the start state was copied to checkpoint 0)
+    const void* in = ck(0);
+    bool gather = false;
+    for (int64_t s = 0; s < N; ++s) {
+      void* out_ = s == N - 1 ? h->f[0] : sg(s & 1);
+      TRY(hlb_launch_step(h, in, out_, gather, t0 + s - 1, st));
+      in = out_;
+      gather = true;
+      if ((s + 1) % K == 0 && (s + 1) / K < nck)
+        TRY(cudaMemcpyAsync(ck((s + 1) / K), out_, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+    }
+    fin_mode = HLB_READ_GATHER_AB;
   } else {
-    TRY(hlb_launch_state(h, W, HLB_READ_GATHER_AA, t0 + N - 1, h->f[0], -1, st));
-    fin_mode = HLB_READ_LOCAL;
+    void* W = sg(0);
+    TRY(cudaMemcpyAsync(W, ck(0), h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+    bool swapped = false;
+    for (int64_t s = 0; s < N; ++s) {
+      TRY(hlb_launch_aa(h, W, swapped, t0 + s, st));
+      swapped = !swapped;
+      if (!swapped && (s + 1) % K == 0 && (s + 1) / K < nck)
+        TRY(cudaMemcpyAsync(ck((s + 1) / K), W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+    }
+    // the final state f(t0 + N) in the AA layout it ended in
+    TRY(cudaMemcpyAsync(h->f[0], W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+    fin_mode = swapped ? HLB_READ_GATHER_AA : HLB_READ_LOCAL;
   }
   const void* fin_state = h->f[0];
 
@@ -574,8 +592,9 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   TRY(launch_probe_adj<S>(h, fin_state, fin_mode, t0 + N - 1, pr, mu[a], jp, st));
   for (int64_t c = nck - 1; c >= 0; --c) {
     const int64_t sb = c * K, se = std::min<int64_t>(N, (c + 1) * K);
+    const bool ck_gather = ab && c > 0;  // checkpoint holds s'(cK - 1)
     const void* rin = ck(c);
-    bool rg = false;
+    bool rg = ck_gather;
     for (int64_t s = sb; s < se; ++s) {
       TRY(hlb_launch_step(h, rin, sg(s - sb), rg, t0 + s - 1, st));
       rin = sg(s - sb);
@@ -583,7 +602,7 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
     }
     for (int64_t s = se - 1; s >= sb; --s) {
       const void* prev = s == sb ? ck(c) : sg(s - sb - 1);
-      const bool gprev = s != sb;  // a segment starts from its pre-collision checkpoint
+      const bool gprev = s != sb || ck_gather;  // f(s) gathered from s'(s - 1), or a checkpoint in place
       // mu(s) = C^T G^T mu(s+1) + dJ/df(s) at the probes (s >= 1), in one pass
       TRY(launch_adjoint<S>(h, prev, gprev, sg(s - sb), mu[a], mu[a ^ 1], t0 + s - 1, t0 + s, pm, dtau_part, dlink,
                             s >= 1, st));
@@ -599,7 +618,7 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
 #undef TRY
   h->cur = 0;
   h->phase = fin_mode;
-  h->stepped = h->scheme == HLB_AA;
+  h->stepped = true;  // the final state came from a step of the solver's scheme
   h->t = t0 + N;
   if (J) *J = host[0];
   if (dtau_out) *dtau_out = host[1];

@@ -36,7 +36,7 @@ int hlb_cuda_fail(cudaError_t e, const char* where) {
 
 extern "C" const char* hlb_last_error(void) { return g_err.c_str(); }
 
-extern "C" int hlb_version(void) { return 10100; }
+extern "C" int hlb_version(void) { return 10200; }
 
 // ---------------------------------------------------------------------------
 // waveforms
@@ -114,7 +114,7 @@ StepParams hlb_solver::params(int64_t tb) const {
 namespace {
 
 struct Layout {
-  size_t f0 = 0, f1 = 0, src = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, icode = 0, ioff = 0,
+  size_t f0 = 0, f1 = 0, src = 0, ctab = 0, tbase = 0, ctflag = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, icode = 0, ioff = 0,
          ilist = 0, mon = 0, wkpar = 0, wkstate = 0,
          ioval = 0, iovnext = 0, total = 0;
   int64_t n_links = 0;
@@ -231,6 +231,9 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.f0 = off; off += state;
   y.f1 = off; off += resolve_scheme(o->scheme, n) == HLB_AA ? 0 : state;
   y.src = off; off += align_up(sizeof(int32_t) * 18 * (size_t)row_stride(n));
+  y.ctab = off; off += align_up(sizeof(uint32_t) * 9 * (size_t)row_stride(n));
+  y.tbase = off; off += align_up(sizeof(int32_t) * hlb::CT_BASES * (size_t)((n + hlb::CT_TILE - 1) / hlb::CT_TILE));
+  y.ctflag = off; off += align_up(sizeof(int32_t));
   y.links = off; off += align_up(sizeof(LinkRec) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.amp = off; off += align_up(sizeof(double) * (size_t)std::max(y.n_groups, 1));
   y.normal = off; off += L->wall_normal ? align_up(sizeof(float) * 3 * (size_t)n) : 0;
@@ -320,6 +323,9 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   h->f[0] = base + y.f0;
   h->f[1] = h->scheme == HLB_AA ? nullptr : base + y.f1;
   h->d_src = (int32_t*)(base + y.src);
+  h->d_ctab = (uint32_t*)(base + y.ctab);
+  h->d_tbase = (int32_t*)(base + y.tbase);
+  int32_t* d_misfit = (int32_t*)(base + y.ctflag);
   h->d_links = (LinkRec*)(base + y.links);
   h->d_amp = (double*)(base + y.amp);
   h->d_normal = L->wall_normal ? (float*)(base + y.normal) : nullptr;
@@ -431,6 +437,12 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   isites.erase(std::unique(isites.begin(), isites.end()), isites.end());
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, st);
+  // compact index table from the re-coded one; the fit flag comes back with
+  // the final synchronisation
+  int32_t misfit = 1;
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_misfit, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = hlb_launch_ctab(h, d_misfit, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&misfit, d_misfit, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess && y.n_links > 0)
     e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(double) * ampf.size(), cudaMemcpyHostToDevice, st);
@@ -472,6 +484,7 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f[0], 0, h->state_bytes(), st);  // rest: h = f - w = 0
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return hlb_cuda_fail(e, "hlb_create upload");  // the owner frees h
+  h->compact = !o->full_index && misfit == 0;
   h->cur = 0;
   h->phase = 0;
   h->t = 0;
@@ -497,6 +510,10 @@ extern "C" int hlb_set_stream(hlb_solver* h, hlb_stream s) {
 }
 
 extern "C" int64_t hlb_n_sites(const hlb_solver* h) { return h ? h->n : -1; }
+extern "C" int hlb_compact_index(const hlb_solver* h) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  return h->compact ? 1 : 0;
+}
 extern "C" int hlb_n_amp_groups(const hlb_solver* h) { return h ? h->n_groups_total : -1; }
 
 extern "C" int hlb_set_tau(hlb_solver* h, double tau) {

@@ -393,4 +393,60 @@ __device__ __forceinline__ const int32_t* idx_at(const int32_t* src, int i, uint
   return WIDE ? src + ((uint64_t)(i - 1) * sn + x) : src + (uint32_t)(i - 1) * sn + x;
 }
 
+// ---------------------------------------------------------------------------
+// Compact index table.  The lattice is ordered lexicographically by (z, y, x)
+// and x - c_i keeps that order, so over a tile of CT_TILE consecutive sites
+// the fluid sources of one direction increase with the site index, and in
+// vessel lattices they span a few hundred sites.  Per tile and direction the
+// table keeps the smallest fluid source (tbase[tile][i - 1], CT_BASES int32
+// entries a tile, the last two unused), and per site and direction a 16-bit
+// offset from it, or CT_WALL / CT_IOLET for a link without a fluid source.
+// Directions 2p + 1 (low half) and 2p + 2 (high half) share one 32-bit word
+// in row p of ctab (rows of stride sn): 36 bytes a site instead of the 72 of
+// the 32-bit table.  A lattice with a span above CT_MAX_SPAN uses the 32-bit
+// table (the same kernels with CT = false).
+// ---------------------------------------------------------------------------
+constexpr uint32_t CT_WALL = 0xffffu, CT_IOLET = 0xfffeu, CT_MAX_SPAN = 0xfffdu;
+constexpr int CT_TILE = 256, CT_BASES = 20;
+
+// How a kernel loads its index entries: read-only cached, streaming (read
+// once, evict first), or cached in L1 for a re-read by the same thread.
+enum { LD_NC = 0, LD_STREAM = 1, LD_L1 = 2 };
+template <int LD, typename T>
+__device__ __forceinline__ T ld_index(const T* p) {
+  return LD == LD_STREAM ? __ldcs(p) : (LD == LD_L1 ? __ldca(p) : __ldg(p));
+}
+
+// The 18 index codes s[i - 1] of site x (tile `tile` of the compact table):
+// a fluid source's index, -1 across a wall, and for an iolet link the
+// re-coded record (32-bit table) or -2 (compact table).
+template <bool CT, bool WIDE, int LD>
+__device__ __forceinline__ void load_codes(const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
+                                           const int32_t* __restrict__ tbase, uint32_t sn, uint32_t x,
+                                           uint32_t tile, int32_t* s) {
+  if (CT) {
+    uint32_t w[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) w[q] = ld_index<LD>(WIDE ? ctab + ((uint64_t)q * sn + x) : ctab + (uint32_t)q * sn + x);
+    const int4* tb = reinterpret_cast<const int4*>(tbase + (uint64_t)tile * CT_BASES);
+    int b[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int4 v = __ldg(tb + q);
+      b[4 * q] = v.x;
+      b[4 * q + 1] = v.y;
+      b[4 * q + 2] = v.z;
+      b[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t o = (i & 1) ? (w[(i - 1) >> 1] & 0xffffu) : (w[(i - 1) >> 1] >> 16);
+      s[i - 1] = o < CT_IOLET ? (int32_t)((uint32_t)b[i - 1] + o) : (o == CT_WALL ? -1 : -2);
+    }
+  } else {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s[i - 1] = ld_index<LD>(idx_at<WIDE>(src, i, sn, x));
+  }
+}
+
 }  // namespace hlb

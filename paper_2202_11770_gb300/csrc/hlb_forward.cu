@@ -8,12 +8,17 @@
 // per-site fix-up.  Two streaming schemes:
 //
 //  * pull A-B (k_step): read buffer A by gathering through the index table,
-//    write buffer B; 224 B per FP32 site update.
+//    write buffer B; 188 B per FP32 site update with the compact index
+//    table (224 B with the int32 one).
 //  * AA pattern (k_aa_even / k_aa_odd, then k_aa_fix over iolet sites): one
 //    buffer.  Even steps read a site's 19 slots and write them back swapped
 //    (no index table); odd steps read 19 slots through the index table and
-//    write the results to the very same 19 slots.  152 B (even) + 224 B
-//    (odd) per FP32 update.
+//    write the results to the very same 19 slots.  152 B (even) + 188 B
+//    (odd; 224 B with the int32 table) per FP32 update.
+//
+// The bulk kernels take the index from its compact form (hlb_common.cuh,
+// built by k_ctab_build) unless the lattice does not fit it; iolet-site
+// paths and read-back kernels use the int32 table.
 //
 // Read modes of the readback kernels: LOCAL (the buffer holds f(t) in place),
 // GATHER_AB (the buffer holds s'(t-1); boundaries applied while gathering),
@@ -95,10 +100,12 @@ __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __
 // iolet sites, a warp each (step_iolet_site); the others take 256 bulk sites,
 // a thread each, and leave iolet sites alone.  The iolet blocks, spread
 // through the grid, run beside the bulk blocks instead of after them.
-// WIDE: offsets within direction pairs (lattices above ~226M sites).
-template <typename S, bool WIDE>
+// WIDE: offsets within direction pairs (lattices above ~226M sites).  CT:
+// bulk codes from the compact index table (iolet warps read the 32-bit one).
+template <typename S, bool WIDE, bool CT>
 __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S* __restrict__ fout,
-                                                const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
+                                                const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
+                                                const int32_t* __restrict__ tbase, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
                                                 int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
                                                 const StepParams p) {
@@ -109,14 +116,17 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
     return;
   }
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
-  const uint32_t x = (b - min(n_iolet_blocks, j + 1)) * BLOCK + threadIdx.x;
+  const uint32_t tile = b - min(n_iolet_blocks, j + 1);
+  const uint32_t x = tile * BLOCK + threadIdx.x;
   if (x >= n) return;
+  int32_t code[Q - 1];
+  load_codes<CT, WIDE, LD_STREAM>(src, ctab, tbase, sn, x, tile, code);
   R h[Q];
   h[0] = ldpop(fin + x);
   bool iolet = false;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int32_t s = ldidx(idx_at<WIDE>(src, i, sn, x));
+    const int32_t s = code[i - 1];
     // fluid source: row i at s; otherwise row opp(i) at x (bounce-back; iolets: step_iolet_site)
     h[i] = ldpop(at<WIDE>(fin, i, n, s >= 0 ? slot<WIDE>(i, n, (uint32_t)s) : slot<WIDE>(opp(i), n, x)));
     iolet |= s <= -2;
@@ -152,7 +162,12 @@ __global__ void __launch_bounds__(BLOCK) k_aa_even(S* A, const StepParams p) {
 }
 
 // Even step for 16-bit storage, two neighbouring sites per thread with 4-byte
-// accesses (rows are 4-byte aligned when n is even).
+// accesses (rows are 4-byte aligned when n is even).  The two collisions run
+// in paired FP32 instructions (collide2), which halves the arithmetic
+// instructions of a kernel whose 16-bit traffic leaves instruction issue as
+// a limit.  Four blocks per SM (64 registers, a few bytes of spill) measured
+// 4-5 % faster than the scalar collisions, and than three blocks without
+// the spill.
 template <typename S> struct Pair;
 template <> struct Pair<__nv_bfloat16> {
   using T = __nv_bfloat162;
@@ -165,8 +180,56 @@ template <> struct Pair<__half> {
   static __device__ __forceinline__ T from(float a, float b) { return __floats2half2_rn(a, b); }
 };
 
+// Paired FP32 arithmetic (sm_100 and later): one instruction applies the
+// operation to .x and .y, each rounded as the scalar operation is.
+__device__ __forceinline__ float2 p_splat(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// collide() of two sites at once, h[i] = (site x, site x + 1).  Directions
+// 2p-1 and 2p are opposite, so each pair shares c.u and 4.5 (c.u)^2 - 1.5 u.u
+// and differs only in the sign of the 3 c.u term.
+__device__ __forceinline__ void collide2(float2* h, float omega) {
+  float2 d = h[0];
+#pragma unroll
+  for (int i = 1; i < Q; ++i) d = p_add(d, h[i]);
+  // momentum: each component is the sum over the pairs that move along it
+  float2 jx = p_sub(h[1], h[2]), jy = p_sub(h[3], h[4]), jz = p_sub(h[5], h[6]);
+#pragma unroll
+  for (int i = 7; i < Q; ++i) {
+    if (cx(i)) jx = cx(i) > 0 ? p_add(jx, h[i]) : p_sub(jx, h[i]);
+    if (cy(i)) jy = cy(i) > 0 ? p_add(jy, h[i]) : p_sub(jy, h[i]);
+    if (cz(i)) jz = cz(i) > 0 ? p_add(jz, h[i]) : p_sub(jz, h[i]);
+  }
+  const float2 rho = p_add(p_splat(1.f), d);
+  const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+  const float2 ux = p_mul(jx, inv), uy = p_mul(jy, inv), uz = p_mul(jz, inv);
+  const float2 nusq = p_mul(p_splat(-1.5f), p_fma(uz, uz, p_fma(uy, uy, p_mul(ux, ux))));
+  const float2 om = p_splat(omega);
+  {  // rest population: c.u = 0
+    const float2 heq = p_mul(p_splat(1.f / 3.f), p_fma(rho, nusq, d));
+    h[0] = p_fma(om, p_sub(heq, h[0]), h[0]);
+  }
+#pragma unroll
+  for (int q = 1; q < 10; ++q) {
+    const int i = 2 * q - 1;  // c_i has a positive first nonzero component
+    float2 cu = cx(i) ? ux : uy;
+    if (cx(i) && cy(i)) cu = cy(i) > 0 ? p_add(ux, uy) : p_sub(ux, uy);
+    if (cx(i) && cz(i)) cu = cz(i) > 0 ? p_add(ux, uz) : p_sub(ux, uz);
+    if (!cx(i) && cz(i)) cu = cy(i) ? (cz(i) > 0 ? p_add(uy, uz) : p_sub(uy, uz)) : uz;
+    const float2 a = p_fma(p_mul(p_splat(4.5f), cu), cu, nusq);
+    const float2 tp = p_fma(p_splat(3.f), cu, a), tm = p_fma(p_splat(-3.f), cu, a);
+    const float2 w = p_splat(wgt<float>(i));
+    const float2 ep = p_mul(w, p_fma(rho, tp, d)), em = p_mul(w, p_fma(rho, tm, d));
+    h[i] = p_fma(om, p_sub(ep, h[i]), h[i]);
+    h[i + 1] = p_fma(om, p_sub(em, h[i + 1]), h[i + 1]);
+  }
+}
+
 template <typename S>
-__global__ void __launch_bounds__(BLOCK) k_aa_even2(S* A, const StepParams p) {
+__global__ void __launch_bounds__(BLOCK, 4) k_aa_even2(S* A, const StepParams p) {
   using P = Pair<S>;
   using T = typename P::T;
   const int64_t n = p.n;
@@ -174,17 +237,12 @@ __global__ void __launch_bounds__(BLOCK) k_aa_even2(S* A, const StepParams p) {
   if (x >= n) return;
   T* A2 = reinterpret_cast<T*>(A);
   const int64_t n2 = n / 2, x2 = x / 2;
-  float a[Q], b[Q];
+  float2 h[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const float2 v = P::to(A2[(int64_t)i * n2 + x2]);
-    a[i] = v.x;
-    b[i] = v.y;
-  }
-  collide<float>(a, float(p.omega));
-  collide<float>(b, float(p.omega));
+  for (int i = 0; i < Q; ++i) h[i] = P::to(A2[(int64_t)i * n2 + x2]);
+  collide2(h, float(p.omega));
 #pragma unroll
-  for (int i = 0; i < Q; ++i) __stcs(A2 + (int64_t)opp(i) * n2 + x2, P::from(a[i], b[i]));
+  for (int i = 0; i < Q; ++i) __stcs(A2 + (int64_t)opp(i) * n2 + x2, P::from(h[i].x, h[i].y));
 }
 
 // Boundary value of iolet link (pull direction i, record L) at a site whose
@@ -276,18 +334,22 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
 // offsets within direction pairs (lattices above ~226M sites), which need a
 // few more registers: four blocks per SM (64 registers) measured 8 % faster
 // than five with their spills.
-template <typename S, bool WIDE>
-__global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int32_t* __restrict__ src, const StepParams p) {
+template <typename S, bool WIDE, bool CT>
+__global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int32_t* __restrict__ src,
+                                                               const uint32_t* __restrict__ ctab,
+                                                               const int32_t* __restrict__ tbase, const StepParams p) {
   using R = typename Real<S>::type;
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
   const uint32_t x = blockIdx.x * BLOCK + threadIdx.x;
   if (x >= n) return;
+  int32_t code[Q - 1];
+  load_codes<CT, WIDE, LD_NC>(src, ctab, tbase, sn, x, blockIdx.x, code);
   uint32_t off[Q];
   R h[Q];
   h[0] = to_real(A[x]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int32_t s = __ldg(idx_at<WIDE>(src, i, sn, x));
+    const int32_t s = code[i - 1];
     // slot opp(i) of the source, or slot i of x itself across a wall or iolet
     off[i] = s >= 0 ? slot<WIDE>(opp(i), n, (uint32_t)s) : slot<WIDE>(i, n, x);
     h[i] = to_real(*at<WIDE>(A, i, n, off[i]));
@@ -296,6 +358,54 @@ __global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int3
   stpop<S>(A + x, h[0]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) stpop<S>(at<WIDE>(A, i, n, off[i]), h[opp(i)]);
+}
+
+// ---------------------------------------------------------------------------
+// Compact index table (layout in hlb_common.cuh), built once from the 32-bit
+// table: one block per tile.  Per direction the block finds the smallest and
+// largest fluid source of its sites (warp min/max, then across the eight
+// warps), writes the base, and each thread its offset; pairs of directions
+// share a word.  Padding entries (n <= x < sn) read as walls.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CT_TILE) k_ctab_build(const int32_t* __restrict__ src, int64_t n, int64_t sn,
+                                                        uint32_t* __restrict__ ctab, int32_t* __restrict__ tbase,
+                                                        int32_t* __restrict__ misfit) {
+  static_assert(CT_TILE == 256, "eight warps a tile");
+  __shared__ uint32_t smin[8], smax[8];
+  const int64_t x = (int64_t)blockIdx.x * CT_TILE + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t word = 0;
+  for (int i = 1; i < Q; ++i) {
+    const int32_t s = x < n ? src[(int64_t)(i - 1) * sn + x] : -1;
+    uint32_t lo = __reduce_min_sync(0xffffffffu, s >= 0 ? (uint32_t)s : 0xffffffffu);
+    uint32_t hi = __reduce_max_sync(0xffffffffu, s >= 0 ? (uint32_t)s : 0u);
+    if (lane == 0) {
+      smin[wid] = lo;
+      smax[wid] = hi;
+    }
+    __syncthreads();
+    lo = smin[0];
+    hi = smax[0];
+    for (int k = 1; k < 8; ++k) {
+      lo = min(lo, smin[k]);
+      hi = max(hi, smax[k]);
+    }
+    __syncthreads();
+    const bool any = lo != 0xffffffffu;  // some site of the tile has a fluid source
+    const uint32_t base = any ? lo : 0u;
+    if (threadIdx.x == 0) {
+      tbase[(int64_t)blockIdx.x * CT_BASES + (i - 1)] = (int32_t)base;
+      if (any && hi - lo > CT_MAX_SPAN) atomicOr(misfit, 1);
+    }
+    const uint32_t o = s >= 0 ? ((uint32_t)s - base) & 0xffffu : (s == -1 ? CT_WALL : CT_IOLET);
+    if (i & 1) {
+      word = o;
+    } else {
+      word |= o << 16;
+      if (x < sn) ctab[(int64_t)(i / 2 - 1) * sn + x] = word;
+    }
+  }
+  if (threadIdx.x < CT_BASES - (Q - 1)) tbase[(int64_t)blockIdx.x * CT_BASES + (Q - 1) + threadIdx.x] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -536,9 +646,10 @@ struct StepOp {
     if (gather) {
       const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // 8 warps (sites) per block
       const unsigned grid = gi + grid_for(h->n);
-      auto kernel = h->off32 ? k_step<S, false> : k_step<S, true>;
-      kernel<<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_links, h->d_amp, h->d_iolet_sites,
-                                    h->n_iolet_sites, gi, gi ? grid / gi : 1, p);
+      auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
+                               : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
+      kernel<<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase, h->d_links, h->d_amp,
+                                    h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, p);
     } else {
       k_step_local<S><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, p);
     }
@@ -570,7 +681,9 @@ struct AAOp {
   static cudaError_t run(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
     StepParams p = h->params(t);
     if (odd)
-      (h->off32 ? k_aa_odd<S, false> : k_aa_odd<S, true>)<<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, p);
+      (h->compact ? (h->off32 ? k_aa_odd<S, false, true> : k_aa_odd<S, true, true>)
+                  : (h->off32 ? k_aa_odd<S, false, false> : k_aa_odd<S, true, false>))
+          <<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, h->d_ctab, h->d_tbase, p);
     else
       aa_even<S>(h, (S*)A, p, s);
     if (h->n_iolet_sites > 0) {
@@ -829,6 +942,11 @@ cudaError_t hlb_launch_monitor(const hlb_solver* h, const void* fin, int mode, i
 cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
                              cudaStream_t s) {
   return dispatch<StateOp>(h->precision, h, fin, mode, tb, out, row, s);
+}
+cudaError_t hlb_launch_ctab(const hlb_solver* h, int32_t* misfit, cudaStream_t s) {
+  const int64_t tiles = (h->sn + CT_TILE - 1) / CT_TILE;
+  k_ctab_build<<<(unsigned)tiles, CT_TILE, 0, s>>>(h->d_src, h->n, h->sn, h->d_ctab, h->d_tbase, misfit);
+  return cudaGetLastError();
 }
 cudaError_t hlb_launch_init(const hlb_solver* h, void* f, double rho0, const float* u0, cudaStream_t s) {
   return dispatch<InitOp>(h->precision, h, f, rho0, u0, s);

@@ -57,6 +57,9 @@ struct hlb_solver {
 
   // device tables (inside the caller's workspace)
   int32_t* d_src = nullptr;           // [18][n], iolet links re-coded to -(2 + record)
+  uint32_t* d_ctab = nullptr;         // compact index table [9][sn] (hlb_common.cuh)
+  int32_t* d_tbase = nullptr;         // its per-tile bases [tiles][CT_BASES]
+  bool compact = false;               // bulk step and adjoint codes from the compact table
   hlb::LinkRec* d_links = nullptr;
   double* d_amp = nullptr;            // [n_groups_total]
   float* d_normal = nullptr;          // [3][n] or null
@@ -131,6 +134,9 @@ cudaError_t hlb_launch_monitor(const hlb_solver* h, const void* fin, int mode, i
 // Shifted pre-collision state into out [19][n] (row < 0) or direction `row` into out [n].
 cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
                              cudaStream_t s);
+// Compact index table from d_src; *misfit (device, zeroed by the caller)
+// becomes nonzero if some tile's sources span more than a 16-bit offset.
+cudaError_t hlb_launch_ctab(const hlb_solver* h, int32_t* misfit, cudaStream_t s);
 // Equilibrium initialisation; u0 [3][n] device or null.
 cudaError_t hlb_launch_init(const hlb_solver* h, void* f, double rho0, const float* u0, cudaStream_t s);
 // Mass (out[0]) and per-iolet flux (out[1..]) in FP64.

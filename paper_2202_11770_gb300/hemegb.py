@@ -52,7 +52,7 @@ class hlb_lattice(C.Structure):
 
 class hlb_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("scheme", C.c_int32), ("ladd_rho_one", C.c_int32),
-                ("ghost_full_u", C.c_int32), ("wide_offsets", C.c_int32)]
+                ("ghost_full_u", C.c_int32), ("wide_offsets", C.c_int32), ("full_index", C.c_int32)]
 
 
 class hlb_waveform(C.Structure):
@@ -75,6 +75,7 @@ _PROTOS = {
     "hlb_set_stream": (C.c_int, [_P, _P]),
     "hlb_n_sites": (C.c_int64, [_P]),
     "hlb_n_amp_groups": (C.c_int, [_P]),
+    "hlb_compact_index": (C.c_int, [_P]),
     "hlb_set_tau": (C.c_int, [_P, C.c_double]),
     "hlb_set_velocity_waveform": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                                             C.POINTER(hlb_waveform)]),
@@ -223,7 +224,7 @@ class Solver:
     """
 
     def __init__(self, lattice, tau=1.0, precision="fp32", scheme="auto", ladd_rho_one=False,
-                 ghost_full_u=False, use_normals=True, stream=None, wide_offsets=False):
+                 ghost_full_u=False, use_normals=True, stream=None, wide_offsets=False, full_index=False):
         torch = _torch()
         lib = library()
         self._torch = torch
@@ -250,7 +251,8 @@ class Solver:
         self._ios = ios
         scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
         self._opt = hlb_options(precision=self.precision, scheme=scheme, ladd_rho_one=int(ladd_rho_one),
-                                ghost_full_u=int(ghost_full_u), wide_offsets=int(wide_offsets))
+                                ghost_full_u=int(ghost_full_u), wide_offsets=int(wide_offsets),
+                                full_index=int(full_index))
         nbytes = hlb_workspace_bytes(self._lat, self._opt)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         base = self.workspace.data_ptr()
@@ -273,6 +275,13 @@ class Solver:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def compact_index(self) -> bool:
+        """True if the step and adjoint kernels read the compact index table."""
+        r = int(self._lib.hlb_compact_index(self._h))
+        _check(min(r, 0))
+        return bool(r)
 
     @property
     def n_groups(self) -> int:

@@ -105,3 +105,31 @@ def test_full_size_adjoint_vs_central_differences():
     for d in dirs:
         fd = (run("fp64", tau, amps + h * d)[0] - run("fp64", tau, amps - h * d)[0]) / (2 * h)
         assert abs(damp @ d - fd) <= 1e-3 * abs(fd), (damp @ d, fd)
+
+
+@pytest.mark.parametrize("scheme", ["ab", "aa"])
+def test_adjoint_leaves_the_forward_state(scheme):
+    """The forward sweep runs the solver's own step kernels: afterwards the
+    solver holds, bit for bit, the state of N plain steps, and stepping on
+    from there matches too."""
+    lat = geo.tree(1, 7, root_radius=4.0, length_ratio=5.0, n_sectors=2, n_rings=2)
+    N = 23                                   # odd: ends mid AA cycle; > one checkpoint interval
+    probe = np.nonzero(lat.xyz[:, 2] == int(lat.info["root_length"] // 2))[0]
+    target = np.full(probe.size, 0.02)
+    amps = np.array([1.0, 0.9, 1.1, 0.95])
+    runs = []
+    for adj in (True, False):
+        s = hemegb.Solver(lat, tau=0.7, precision="fp32", scheme=scheme)
+        _setup(s, lat, amps)
+        if adj:
+            s.adjoint(N, probe, target, [0, 0, 1])
+        else:
+            s.step(N)
+        f, t = s.state()
+        m, q = s.reduce()
+        s.step(5)
+        runs.append((f, t, m, q, s.state()[0]))
+    (fa, ta, ma, qa, ga), (fb, tb, mb, qb, gb) = runs
+    assert ta == tb == N
+    assert fa.tobytes() == fb.tobytes() and ga.tobytes() == gb.tobytes()
+    assert ma == mb and np.array_equal(qa, qb)
