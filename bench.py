@@ -74,10 +74,12 @@ CTYPE = {"fp32": "float", "bf16": "__nv_bfloat16", "fp16": "__half", "fp64": "do
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": "7adcbba9671fe08a",
-           # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site tree
-           "bytes_per_site": {"k_aa_odd": (2960304128 + 1488711424) / 20000864,
-                              "k_step": (3050549504 + 1482938624) / 20000864}}
+TRAFFIC = {"sha": "a69e8170eaf367f9",
+           # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site
+           # tree, kernels on the compact index table
+           "index": "compact",
+           "bytes_per_site": {"k_aa_odd": (2246435840 + 1473382912) / 20000864,
+                              "k_step": (2337090048 + 1483820288) / 20000864}}
 
 
 def kernel_sha() -> str:
@@ -424,7 +426,8 @@ def run_ours(args):
     kname = kernel_names(n)[0 if scheme == "ab" else 1]
     kst = head["kernels"][kname]
     traffic = None
-    if TRAFFIC["sha"] == kernel_sha() and compact and kname in TRAFFIC["bytes_per_site"]:
+    if (TRAFFIC["sha"] == kernel_sha() and TRAFFIC["index"] == ("compact" if compact else "int32")
+            and kname in TRAFFIC["bytes_per_site"]):
         traffic = TRAFFIC["bytes_per_site"][kname] * n
 
     forms = {f"{prec0}_{scheme}": head}
