@@ -77,3 +77,31 @@ def test_tree_amplitude_groups():
     assert g.min() == 0 and g.max() == 63
     counts = np.bincount(g, minlength=64)
     assert (counts > 0).all()
+
+
+@pytest.mark.parametrize("depth,seed,sites", [(2, 2202, 50_000), (4, 11770, 300_000)])
+def test_tile_sources_increase_and_fit_16_bits(depth, seed, sites):
+    """The step kernels' compact index table rests on two properties of the
+    (z, y, x) site order: over a 256-site tile the fluid sources of one
+    direction increase with the site index, and they span fewer than 65,534
+    sites (here a few hundred), so 16-bit offsets from a per-tile base
+    reach them all."""
+    lat = geo.tree(depth, seed, target_sites=sites, length_ratio=5.0)
+    n, T = lat.n, 256
+    order = np.lexsort((lat.xyz[:, 0], lat.xyz[:, 1], lat.xyz[:, 2]))
+    assert np.array_equal(order, np.arange(n))          # sites sorted by (z, y, x)
+    tile = np.arange(n) // T
+    worst = 0
+    for i in range(18):
+        s = lat.src[i].astype(np.int64)
+        x = np.nonzero(s >= 0)[0]
+        same = tile[x[1:]] == tile[x[:-1]]
+        assert (s[x[1:]][same] > s[x[:-1]][same]).all()  # increasing within a tile
+        lo = np.full(tile[-1] + 1, np.iinfo(np.int64).max)
+        hi = np.full(tile[-1] + 1, -1)
+        np.minimum.at(lo, tile[x], s[x])
+        np.maximum.at(hi, tile[x], s[x])
+        has = hi >= 0
+        worst = max(worst, int((hi[has] - lo[has]).max()))
+    assert worst <= 65533
+    assert worst < 4 * T
