@@ -303,6 +303,10 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   h->off32 = !o->wide_offsets && (uint64_t)Q * (uint64_t)h->sn <= 0xffffffffull;
   h->stream = (cudaStream_t)stream;
   h->device = attr.device;
+  if (cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, attr.device) != cudaSuccess) {
+    cudaGetLastError();
+    h->n_sm = 0;  // no prefetch distance: the kernels skip the prefetch
+  }
   h->has_normals = L->wall_normal != nullptr;
   h->wave.resize(h->n_iolets);
   h->group_offset.assign(h->n_iolets, -1);

@@ -38,6 +38,45 @@ constexpr int BLOCK = 256;
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
+// L2 prefetch hint: `bytes` (a multiple of 16) from a 16-byte aligned address.
+__device__ __forceinline__ void l2_prefetch(const void* q, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(q)), "r"(bytes)
+               : "memory");
+}
+
+// Called by the first warp of a bulk block: prefetch into L2 what the block
+// that takes tile `tile` (about one wave of resident blocks later) reads
+// first, so that its loads find L2 instead of waiting on DRAM.  Lanes 0-8:
+// the tile's compact index words (row q, 256 sites).  With POPS, lanes
+// 9-26: for direction i = lane - 8, the population row its gathers read
+// (ROWOPP: row opp(i), as the AA odd step reads; else row i) from the
+// tile's base for i, 320 sites wide (the sources of a tile span about 255
+// sites on vessel lattices).  Every range is clamped to its array: ctab
+// holds 9 rows of sn words, A 19 rows of n populations.
+template <typename S, bool POPS, bool ROWOPP>
+__device__ __forceinline__ void prefetch_tile(const S* A, const uint32_t* __restrict__ ctab,
+                                              const int32_t* __restrict__ tbase, uint32_t n, uint32_t sn,
+                                              uint32_t tile) {
+  const uint32_t ntiles = (n + BLOCK - 1) / BLOCK;
+  const int l = threadIdx.x & 31;
+  if (tile >= ntiles) return;
+  const uint64_t x0 = (uint64_t)tile * BLOCK;
+  if (l < 9) {
+    const uint64_t e = x0 + BLOCK < (uint64_t)sn ? x0 + BLOCK : (uint64_t)sn;  // sn: a multiple of 4
+    l2_prefetch(ctab + (uint64_t)l * sn + x0, (uint32_t)((e - x0) * 4));
+  } else if (POPS && l < 9 + Q - 1) {
+    const int i = l - 8;
+    const uint64_t b = (uint32_t)__ldg(tbase + (uint64_t)tile * CT_BASES + (i - 1));  // < n
+    const uint64_t r = ROWOPP ? (uint64_t)lane_opp(i) : (uint64_t)i;
+    const uint64_t e = b + 320 < (uint64_t)n ? b + 320 : (uint64_t)n;
+    const uint64_t total = ((uint64_t)Q * n * sizeof(S) + 15) & ~15ull;  // within the 256-aligned section
+    const uint64_t lo = ((r * n + b) * sizeof(S)) & ~15ull;
+    const uint64_t hr = ((r * n + e) * sizeof(S) + 15) & ~15ull;
+    const uint64_t hi = hr < total ? hr : total;
+    if (hi > lo) l2_prefetch(reinterpret_cast<const char*>(A) + lo, (uint32_t)(hi - lo));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Pull A-B step from f(t) held in place (the first step after initialisation
 // or set_state): no gather.
@@ -108,7 +147,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
                                                 const int32_t* __restrict__ tbase, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
                                                 int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
-                                                const StepParams p) {
+                                                uint32_t pf, const StepParams p) {
   using R = typename Real<S>::type;
   const unsigned b = blockIdx.x, j = b / stride;
   if (b % stride == 0 && j < n_iolet_blocks) {
@@ -118,6 +157,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
   const uint32_t tile = b - min(n_iolet_blocks, j + 1);
   const uint32_t x = tile * BLOCK + threadIdx.x;
+  if (CT && pf && threadIdx.x < 32) prefetch_tile<S, sizeof(S) >= 4, false>(fin, ctab, tbase, n, sn, tile + pf);
   if (x >= n) return;
   int32_t code[Q - 1];
   load_codes<CT, WIDE, LD_STREAM>(src, ctab, tbase, sn, x, tile, code);
@@ -337,10 +377,12 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
 template <typename S, bool WIDE, bool CT>
 __global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int32_t* __restrict__ src,
                                                                const uint32_t* __restrict__ ctab,
-                                                               const int32_t* __restrict__ tbase, const StepParams p) {
+                                                               const int32_t* __restrict__ tbase, uint32_t pf,
+                                                               const StepParams p) {
   using R = typename Real<S>::type;
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
   const uint32_t x = blockIdx.x * BLOCK + threadIdx.x;
+  if (CT && pf && threadIdx.x < 32) prefetch_tile<S, sizeof(S) >= 4, true>(A, ctab, tbase, n, sn, blockIdx.x + pf);
   if (x >= n) return;
   int32_t code[Q - 1];
   load_codes<CT, WIDE, LD_NC>(src, ctab, tbase, sn, x, blockIdx.x, code);
@@ -649,7 +691,8 @@ struct StepOp {
       auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
                                : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
       kernel<<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase, h->d_links, h->d_amp,
-                                    h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, p);
+                                    h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1,
+                                    (uint32_t)h->n_sm * 5u, p);
     } else {
       k_step_local<S><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, p);
     }
@@ -683,7 +726,8 @@ struct AAOp {
     if (odd)
       (h->compact ? (h->off32 ? k_aa_odd<S, false, true> : k_aa_odd<S, true, true>)
                   : (h->off32 ? k_aa_odd<S, false, false> : k_aa_odd<S, true, false>))
-          <<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, h->d_ctab, h->d_tbase, p);
+          <<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, h->d_ctab, h->d_tbase,
+                                            (uint32_t)h->n_sm * (h->off32 ? 5u : 4u), p);
     else
       aa_even<S>(h, (S*)A, p, s);
     if (h->n_iolet_sites > 0) {

@@ -46,6 +46,7 @@ struct hlb_solver {
   // state
   cudaStream_t stream = nullptr;
   int device = 0;
+  int n_sm = 0;                       // SMs of the device: one wave = n_sm x resident blocks per SM
   void* f[2] = {nullptr, nullptr};    // population buffers [19][n] (storage precision); AA uses f[0]
   int cur = 0;                        // buffer holding the current state
   int phase = 0;                      // HLB_READ_LOCAL: f(t) in place; GATHER_AB: s'(t-1); GATHER_AA: AA after an even step
