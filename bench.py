@@ -74,12 +74,12 @@ CTYPE = {"fp32": "float", "bf16": "__nv_bfloat16", "fp16": "__half", "fp64": "do
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": "a69e8170eaf367f9",
+TRAFFIC = {"sha": "cfe99a89aad5f36e",
            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site
-           # tree, kernels on the compact index table
+           # tree, kernels on the compact index table with the one-wave L2 prefetch
            "index": "compact",
-           "bytes_per_site": {"k_aa_odd": (2246435840 + 1473382912) / 20000864,
-                              "k_step": (2337090048 + 1483820288) / 20000864}}
+           "bytes_per_site": {"k_aa_odd": (2327549184 + 1475372032) / 20000864,
+                              "k_step": (2428723968 + 1485461504) / 20000864}}
 
 
 def kernel_sha() -> str:
