@@ -58,7 +58,7 @@ def test_workspace_size_and_validation():
     opt = hemegb.hlb_options(precision=hemegb.HLB_FP32, scheme=hemegb.HLB_PULL_AB)
     nb = hemegb.hlb_workspace_bytes(L, opt)
     n = lat.n
-    assert nb >= 2 * 19 * 4 * n + 18 * 4 * n
+    assert nb >= 2 * 19 * 4 * n + 18 * 4 * n + 9 * 4 * n    # two buffers, int32 table, compact table
     opt16 = hemegb.hlb_options(precision=hemegb.HLB_BF16, scheme=hemegb.HLB_PULL_AB)
     assert hemegb.hlb_workspace_bytes(L, opt16) < nb
 
@@ -108,3 +108,32 @@ def test_lattice_size_limits():
                                iolets=None)
         assert lib.hlb_workspace_bytes(C.byref(L), C.byref(opt), C.byref(out)) == hemegb.HLB_ERR_ARG
         assert b"n_sites" in lib.hlb_last_error()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the public structs have the sizes and field
+    offsets a C compiler gives the header's definitions."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"hlb_iolet": hemegb.hlb_iolet, "hlb_lattice": hemegb.hlb_lattice,
+               "hlb_options": hemegb.hlb_options, "hlb_waveform": hemegb.hlb_waveform,
+               "hlb_objective": hemegb.hlb_objective}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "hemegb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", f"-I{INCLUDE}", str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, f"{name}.{field}"
