@@ -140,7 +140,8 @@ __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __
 // a thread each, and leave iolet sites alone.  The iolet blocks, spread
 // through the grid, run beside the bulk blocks instead of after them.
 // WIDE: offsets within direction pairs (lattices above ~226M sites).  CT:
-// bulk codes from the compact index table (iolet warps read the 32-bit one).
+// bulk codes from the compact index table (iolet warps read the 32-bit one),
+// and an L2 prefetch of the bulk tile `pf` tiles ahead, as in k_aa_odd.
 template <typename S, bool WIDE, bool CT>
 __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S* __restrict__ fout,
                                                 const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
@@ -373,7 +374,10 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
 // (48 registers, a few bytes of spill in FP32) measured fastest.  WIDE:
 // offsets within direction pairs (lattices above ~226M sites), which need a
 // few more registers: four blocks per SM (64 registers) measured 8 % faster
-// than five with their spills.
+// than five with their spills.  CT: codes from the compact index table, and
+// the first warp prefetches into L2 the tile `pf` blocks ahead (one wave of
+// resident blocks; 0: none): index words, and for 4- and 8-byte storage the
+// gathered rows (for 16-bit storage the rows measured slower).
 template <typename S, bool WIDE, bool CT>
 __global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int32_t* __restrict__ src,
                                                                const uint32_t* __restrict__ ctab,
