@@ -328,6 +328,20 @@ def test_16bit_one_step_within_storage_rounding(d3q19, prec, scheme, wide):
     _one_step_within_rounding(lat, 0.55, bc, prec, scheme, w, wide=wide)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_16bit_two_site_even_step_within_storage_rounding(d3q19, pipe, prec):
+    """Even n (the 12,352-site pipe): the AA even step takes two sites per
+    thread and runs their collisions in paired FP32 instructions; both AA
+    parities stay within storage rounding of the oracle's step."""
+    _, w = d3q19
+    assert pipe.n % 2 == 0 and pipe.n % 256
+
+    def bc(x):
+        x.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 200.0})
+        x.set_pressure(1, 1.0)
+    _one_step_within_rounding(pipe, 0.55, bc, prec, "aa", w)
+
+
 def test_invalid_arguments(pipe):
     s = hemegb.Solver(pipe, tau=0.8)
     with pytest.raises(hemegb.HlbError):
