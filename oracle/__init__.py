@@ -16,7 +16,11 @@ Every function here is pinned by the tests in ``tests/test_oracle_*.py``
 against closed forms and invariants (moment identities, rest state, exact
 mass conservation, Poiseuille and Womersley flow, the Poiseuille wall shear
 stress, hand-enumerated streaming, central finite differences for the
-adjoint).
+adjoint).  The Ladd velocity iolet is pinned by the uniform flow it must keep
+exactly, by a one-step enumeration of its link-midpoint weights, and by the
+steady inlet flux and near-inlet profile against the imposed parabola; the
+wall-shear-stress fallback normal by flat faces and box edges
+(``tests/test_oracle_ladd.py``, ``tests/test_oracle_flow.py``).
 """
 from __future__ import annotations
 

@@ -9,6 +9,10 @@ Pins (paper Eqs. 3-8, Section 2.3, Section 6 pipe):
   * steady mass flux is continuous: inlet flux = - outlet flux = mid-plane
     sum of rho u_z;
   * pressure-driven flux is linear in the density difference;
+  * the steady inlet mass flux approaches the integral rho A pi R^2 / 2 of the
+    imposed Ladd profile A (1 - r^2/R^2) (Section 2.3.2, Section 6), closer at
+    R = 12 than at R = 8, and the velocity on the first fluid plane is that
+    profile;
   * WSS cross-section mean matches rho nu |du/dr| of the Poiseuille fit at
     the wall sites' radii within 10 %, closer at higher resolution;
   * oscillating pressure drive reproduces the Womersley profile (alpha = 2).
@@ -24,12 +28,13 @@ from helpers import CS2, density_gradient, fit_parabola, womersley_profile
 
 TAU = 0.8
 NU = (TAU - 0.5) / 3.0
+A_IN = 0.01            # inlet amplitude of the velocity-driven pipes
 
 
 def _velocity_driven(R, L, steps):
     lat = geo.pipe(R, L)
     o = oracle.Oracle(lat, tau=TAU)
-    o.set_velocity(0, [1.0], 0.01)
+    o.set_velocity(0, [1.0], A_IN)
     o.set_pressure(1, 1.0)
     o.init_equilibrium()
     o.step(steps)
@@ -85,6 +90,27 @@ def test_steady_flux_continuity(pipe8):
     assert abs(fl[0] + fl[1]) < 1e-4 * fl[0]
     sel = _midplane(lat, 32)
     assert abs((rho[sel] * u[sel, 2]).sum() / fl[0] - 1) < 0.005
+
+
+def test_ladd_inlet_flux_matches_profile_integral(pipe8, pipe12):
+    dev = []
+    for lat, o, rho, u, _ in (pipe8, pipe12):
+        R = lat.info["radius"]
+        first = lat.xyz[:, 2] == 0
+        dev.append(o.flux()[0] / (rho[first].mean() * A_IN * math.pi * R * R / 2) - 1)
+    assert abs(dev[0]) < 0.01
+    assert abs(dev[1]) < 0.7 * abs(dev[0])
+
+
+def test_ladd_near_inlet_profile(pipe8, pipe12):
+    for (lat, o, rho, u, _), tol in ((pipe8, 0.015), (pipe12, 0.008)):
+        R = lat.info["radius"]
+        first = lat.xyz[:, 2] == 0
+        r = np.hypot(lat.xyz[first, 0], lat.xyz[first, 1])
+        imposed = A_IN * np.clip(1 - r ** 2 / R ** 2, 0, None)
+        assert np.linalg.norm(u[first, 2] - imposed) / np.linalg.norm(imposed) < tol
+        U, R_fit, _, _ = fit_parabola(r, u[first, 2])
+        assert abs(U / A_IN - 1) < 0.005 and abs(R_fit / R - 1) < 0.005
 
 
 def test_pressure_driven_linear():

@@ -15,6 +15,9 @@ ROOT = Path(__file__).resolve().parent.parent
 SRC = ROOT / "oracle" / "oracle.c"
 
 FAST = ["tests/test_oracle_equilibrium.py", "tests/test_oracle_kinematics.py", "tests/test_oracle_adjoint.py"]
+LADD = ["tests/test_oracle_ladd.py"]
+LADD_FLOW = ["tests/test_oracle_flow.py::test_ladd_inlet_flux_matches_profile_integral",
+             "tests/test_oracle_flow.py::test_ladd_near_inlet_profile"]
 
 # (name, original text, mutated text, pins that must catch it)
 MUTANTS = [
@@ -30,6 +33,18 @@ MUTANTS = [
      "dtau += lam[i] * (f[i] - feq[i]) / tau;", FAST),
     ("WSS with (1 - 1/tau)", "-(1.0 - 1.0 / (2.0 * o->tau))", "-(1.0 - 1.0 / o->tau)",
      ["tests/test_oracle_flow.py::test_wss_poiseuille"]),
+    ("Ladd correction without the factor 2", "val = fp[i] - 2.0 * weight(i) * r * cu_w / CS2;",
+     "val = fp[i] - weight(i) * r * cu_w / CS2;", LADD),
+    ("Ladd correction over cs^4", "val = fp[i] - 2.0 * weight(i) * r * cu_w / CS2;",
+     "val = fp[i] - 2.0 * weight(i) * r * cu_w / (CS2 * CS2);", LADD),
+    ("Ladd density fixed at 1", "double r = o->ladd_rho_one ? 1.0 : rho;\n          val = fp[i]",
+     "double r = 1.0;\n          val = fp[i]", LADD),
+    ("Ladd weight at the site, not the link midpoint", "m[a] = p[a] + 0.5 * CV[i][a];", "m[a] = p[a];", LADD),
+    ("Ladd weight with the diameter as radius", "r2 / (io->R * io->R)", "r2 / (4.0 * io->R * io->R)", LADD),
+    ("Ladd correction without the factor 2 (flow pins)", "val = fp[i] - 2.0 * weight(i) * r * cu_w / CS2;",
+     "val = fp[i] - weight(i) * r * cu_w / CS2;", LADD_FLOW),
+    ("Ladd weight at the site (flow pins)", "m[a] = p[a] + 0.5 * CV[i][a];", "m[a] = p[a];", LADD_FLOW),
+    ("WSS fallback normal not normalised", "nv[a] = l > 0 ? nsum[a] / l : 0;", "nv[a] = nsum[a];", LADD),
     ("ghost velocity not projected on the normal", "for (int a = 0; a < 3; ++a) ug[a] = un * io->nrm[a];",
      "for (int a = 0; a < 3; ++a) ug[a] = un * io->nrm[a] + u[a];",
      ["tests/test_oracle_flow.py::test_pressure_driven_linear"]),
@@ -53,7 +68,7 @@ def _run_pins(lib, pins):
 
 def test_clean_oracle_passes_selected_pins(tmp_path):
     lib = _build(SRC.read_text(), tmp_path / "clean.c")
-    rc, out = _run_pins(lib, FAST)
+    rc, out = _run_pins(lib, FAST + LADD + LADD_FLOW)
     assert rc == 0, out
 
 
