@@ -100,7 +100,7 @@ __device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const
                                                typename Real<S>::type (*neq)[BLOCK]) {
   using R = typename Real<S>::type;
   const uint32_t n = (uint32_t)ap.prev.n, sn = (uint32_t)ap.prev.sn, xi = (uint32_t)x;
-  const R omega = R(ap.prev.omega);
+  const R omega = omega_of<R>(ap.prev);
   double dtau_local = 0;
   bool iolet = x >= ap.prev.n;
   Macro<R> m;
@@ -230,7 +230,7 @@ __device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev,
       const R ux = jx / rp, uy = jy / rp, uz = jz / rp;
       if (code <= -2) {
         const LinkRec L = links[-code - 2];
-        const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+        const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
         h = lane_iolet_value<R>(i, L, h, rp, ux, uy, uz, a, p);
       }
     } else if (dir) {
@@ -301,7 +301,7 @@ __device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev,
       m.uz = jz * inv;
     }
     const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-    const R omega = R(p.omega);
+    const R omega = omega_of<R>(p);
     const R cu = lane_cdotu<R>(i, m.ux, m.uy, m.uz);
     const R wi = lane_w<R>(i);
     const R b = lam * wi * (R(3) + R(9) * cu);

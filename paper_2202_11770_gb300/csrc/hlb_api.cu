@@ -92,18 +92,24 @@ StepParams hlb_solver::params(int64_t tb) const {
   p.n = n;
   p.sn = sn;
   p.omega = 1.0 / tau;
+  p.omegaf = (float)p.omega;
   p.n_iolets = n_iolets;
   p.ladd_rho_one = ladd_rho_one;
   p.ghost_full_u = ghost_full_u;
   p.ioval = d_ioval;
   for (int k = 0; k < n_iolets; ++k)
     if (k < (int)wk_on.size() && wk_on[k]) p.coupled[k >> 6] |= 1ull << (k & 63);
+  p.ampf = d_ampf;
   for (int k = 0; k < n_iolets; ++k) {
     p.io[k].nx = iolets[k].normal[0];
     p.io[k].ny = iolets[k].normal[1];
     p.io[k].nz = iolets[k].normal[2];
     double w = wave[k].at((double)tb);
     p.io[k].val = iolets[k].kind == HLB_VELOCITY ? w : w - 1.0;
+    p.io[k].nxf = (float)p.io[k].nx;
+    p.io[k].nyf = (float)p.io[k].ny;
+    p.io[k].nzf = (float)p.io[k].nz;
+    p.io[k].valf = (float)p.io[k].val;
   }
   return p;
 }
@@ -114,7 +120,7 @@ StepParams hlb_solver::params(int64_t tb) const {
 namespace {
 
 struct Layout {
-  size_t f0 = 0, f1 = 0, src = 0, ctab = 0, tbase = 0, ctflag = 0, links = 0, amp = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, icode = 0, ioff = 0,
+  size_t f0 = 0, f1 = 0, src = 0, ctab = 0, tbase = 0, ctflag = 0, links = 0, amp = 0, ampf = 0, normal = 0, stage = 0, red = 0, lflux = 0, isites = 0, icode = 0, imask = 0, ioff = 0,
          ilist = 0, mon = 0, wkpar = 0, wkstate = 0,
          ioval = 0, iovnext = 0, total = 0;
   int64_t n_links = 0;
@@ -236,12 +242,14 @@ Layout layout(const hlb_lattice* L, const hlb_options* o, const std::vector<int6
   y.ctflag = off; off += align_up(sizeof(int32_t));
   y.links = off; off += align_up(sizeof(LinkRec) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.amp = off; off += align_up(sizeof(double) * (size_t)std::max(y.n_groups, 1));
+  y.ampf = off; off += align_up(sizeof(float) * (size_t)std::max(y.n_groups, 1));
   y.normal = off; off += L->wall_normal ? align_up(sizeof(float) * 3 * (size_t)n) : 0;
   y.stage = off; off += align_up(sizeof(float) * 5 * (size_t)n);
   y.red = off; off += align_up(sizeof(double) * (size_t)hlb_reduce_slots(n, L->n_iolets));
   y.lflux = off; off += align_up(sizeof(double) * (size_t)std::max<int64_t>(y.n_links, 1));
   y.isites = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(n_iolet_sites, 1));
   y.icode = off; off += align_up(sizeof(int32_t) * 18 * (size_t)std::max<int64_t>(n_iolet_sites, 1));
+  y.imask = off; off += align_up(sizeof(uint32_t) * (size_t)((n + 31) / 32));
   y.ioff = off; off += align_up(sizeof(int64_t) * (size_t)(L->n_iolets + 1));
   y.ilist = off; off += align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(y.n_links, 1));  // >= sites per iolet
   y.mon = off; off += align_up(sizeof(double) * 2 * (size_t)std::max(L->n_iolets, 1));
@@ -332,6 +340,7 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   int32_t* d_misfit = (int32_t*)(base + y.ctflag);
   h->d_links = (LinkRec*)(base + y.links);
   h->d_amp = (double*)(base + y.amp);
+  h->d_ampf = (float*)(base + y.ampf);
   h->d_normal = L->wall_normal ? (float*)(base + y.normal) : nullptr;
   h->d_stage = (float*)(base + y.stage);
   h->d_red = (double*)(base + y.red);
@@ -339,6 +348,7 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   h->d_lflux = (double*)(base + y.lflux);
   h->d_iolet_sites = (int32_t*)(base + y.isites);
   h->d_icode = (int32_t*)(base + y.icode);
+  h->d_imask = (uint32_t*)(base + y.imask);
   h->d_ioff = (int64_t*)(base + y.ioff);
   h->d_ilist = (int32_t*)(base + y.ilist);
   h->d_mon = (double*)(base + y.mon);
@@ -409,7 +419,6 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
       R.kind = (int8_t)io.kind;
       R.iolet = (int16_t)k;
       R.group = io.kind == HLB_VELOCITY ? h->group_offset[k] + gl : -1;
-      R.pad = 0;
       R.coef = 0.0;
       if (io.kind == HLB_VELOCITY) {
         // Ladd weight at the link midpoint x - c_j / 2
@@ -426,6 +435,7 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
         // f_j(x) = f'_jbar(x) - 2 w rho (c_jbar . u_w) / cs2 = f'_jbar(x) + 6 w_j rho A W (c_j . n)
         R.coef = 6.0 * wgt<double>(j) * W * cn;
       }
+      R.coef_f = (float)R.coef;
       src[(size_t)(j - 1) * sn + x] = -(int32_t)(2 + r);
     }
   }
@@ -450,6 +460,7 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   if (e == cudaSuccess && y.n_links > 0)
     e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(double) * ampf.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ampf, 0, sizeof(float) * ampf.size(), st);
   if (e == cudaSuccess && h->d_normal)
     e = cudaMemcpyAsync(h->d_normal, L->wall_normal, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
@@ -462,6 +473,11 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
     for (int64_t q = 0; q < nis; ++q) icode[(size_t)(i - 1) * nis + q] = src[(size_t)(i - 1) * sn + isites[q]];
   if (e == cudaSuccess && nis > 0)
     e = cudaMemcpyAsync(h->d_icode, icode.data(), sizeof(int32_t) * icode.size(), cudaMemcpyHostToDevice, st);
+  // bit mask of the sites with an iolet link (bulk threads of k_step leave them to the iolet warps)
+  std::vector<uint32_t> imask((size_t)((n + 31) / 32), 0u);
+  for (int32_t x : isites) imask[(size_t)x >> 5] |= 1u << (x & 31);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->d_imask, imask.data(), sizeof(uint32_t) * imask.size(), cudaMemcpyHostToDevice, st);
   // sites of each iolet (a link to it), ascending, as ranges of one list
   std::vector<std::vector<int32_t>> per_io((size_t)h->n_iolets);
   for (int32_t x : isites) {
@@ -539,8 +555,14 @@ static int hlb_set_velocity_waveform_impl(hlb_solver* h, int32_t k, const double
   for (int gi = 0; gi < n_groups; ++gi)
     if (!std::isfinite(amp[gi])) return hlb_fail(HLB_ERR_ARG, "non-finite amplitude");
   h->wave[k] = hw;
-  for (int gi = 0; gi < n_groups; ++gi) h->amp[h->group_offset[k] + gi] = amp[gi];
+  std::vector<float> af((size_t)n_groups);
+  for (int gi = 0; gi < n_groups; ++gi) {
+    h->amp[h->group_offset[k] + gi] = amp[gi];
+    af[(size_t)gi] = (float)amp[gi];
+  }
   CUDA_TRY(cudaMemcpyAsync(h->d_amp + h->group_offset[k], amp, sizeof(double) * n_groups,
+                           cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->d_ampf + h->group_offset[k], af.data(), sizeof(float) * n_groups,
                            cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return HLB_OK;

@@ -85,7 +85,7 @@ struct LinkRec {
   int8_t kind;     // 0 velocity, 1 pressure
   int16_t iolet;
   int32_t group;   // global amplitude group (velocity), -1 otherwise
-  int32_t pad;
+  float coef_f;    // (float) coef, rounded on the host
   double coef;     // velocity: 6 w_j W(x_m) (c_j . n); pressure: unused
 };
 static_assert(sizeof(LinkRec) == 24, "LinkRec is 24 bytes");
@@ -97,6 +97,7 @@ constexpr int MAX_IOLETS = 128;
 struct IoletParam {
   double nx, ny, nz;
   double val;  // velocity iolet: waveform factor w(t); pressure iolet: rho(t) - 1
+  float nxf, nyf, nzf, valf;  // the same rounded to float on the host
 };
 
 struct StepParams {
@@ -106,18 +107,50 @@ struct StepParams {
   int32_t n_iolets;
   int32_t ladd_rho_one;
   int32_t ghost_full_u;
-  int32_t pad;
+  float omegaf;         // (float) omega, rounded on the host: FP64 arithmetic is slow on GB300
+                        // (1/64 of the FP32 rate), so FP32 kernels convert no double per thread
   uint64_t coupled[MAX_IOLETS / 64];  // bit k: iolet k's value lives in ioval[k] (Windkessel outlet)
   const double* ioval;                // device, [n_iolets]: rho - 1 of coupled outlets
+  const float* ampf;                  // device, [amplitude groups]: the amplitudes rounded to float
   IoletParam io[MAX_IOLETS];
 };
 static_assert(MAX_IOLETS % 64 == 0, "coupling mask words");
+
+// Relaxation rate 1/tau in the arithmetic type of a kernel.
+template <typename R> __device__ __forceinline__ R omega_of(const StepParams& p);
+template <> __device__ __forceinline__ float omega_of<float>(const StepParams& p) { return p.omegaf; }
+template <> __device__ __forceinline__ double omega_of<double>(const StepParams& p) { return p.omega; }
 
 // Boundary value of iolet k for this launch: the host waveform, or for a
 // Windkessel outlet the ghost density the device-side model last produced.
 __device__ __forceinline__ double io_val(const StepParams& p, int k) {
   return ((p.coupled[k >> 6] >> (k & 63)) & 1ull) ? p.ioval[k] : p.io[k].val;
 }
+
+// Boundary data in the arithmetic type R of a kernel.  FP32 kernels read
+// copies rounded to float on the host (or, for a Windkessel outlet's ghost
+// density, once on the device): the value is the one R(x) would give, without
+// a conversion from double per use (FP64 arithmetic runs at 1/64 of the FP32
+// rate on GB300).
+template <typename R> struct BC;
+template <> struct BC<float> {
+  static __device__ __forceinline__ float val(const StepParams& p, int k) {
+    return ((p.coupled[k >> 6] >> (k & 63)) & 1ull) ? (float)p.ioval[k] : p.io[k].valf;
+  }
+  static __device__ __forceinline__ float coef(const LinkRec& L) { return L.coef_f; }
+  static __device__ __forceinline__ float amp(const StepParams& p, const double*, int g) { return p.ampf[g]; }
+  static __device__ __forceinline__ float nx(const IoletParam& q) { return q.nxf; }
+  static __device__ __forceinline__ float ny(const IoletParam& q) { return q.nyf; }
+  static __device__ __forceinline__ float nz(const IoletParam& q) { return q.nzf; }
+};
+template <> struct BC<double> {
+  static __device__ __forceinline__ double val(const StepParams& p, int k) { return io_val(p, k); }
+  static __device__ __forceinline__ double coef(const LinkRec& L) { return L.coef; }
+  static __device__ __forceinline__ double amp(const StepParams&, const double* a, int g) { return a[g]; }
+  static __device__ __forceinline__ double nx(const IoletParam& q) { return q.nx; }
+  static __device__ __forceinline__ double ny(const IoletParam& q) { return q.ny; }
+  static __device__ __forceinline__ double nz(const IoletParam& q) { return q.nz; }
+};
 
 // ---------------------------------------------------------------------------
 // Moments and equilibrium in shifted form.
@@ -166,13 +199,64 @@ __device__ __forceinline__ R heq(int i, R drho, R rho, R ux, R uy, R uz, R usq15
   return wgt<R>(i) * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
 }
 
-// BGK collision in place: h <- h + omega (heq - h)   (Eq. 3a, dt = 1).
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// BGK collision (Eq. 3a, dt = 1): h'_i = h_i + omega (heq_i - h_i), handed to
+// emit(i, h'_i) direction by direction as each value is final.  Arranged by
+// opposite pairs (2p+1, 2p+2), whose c.u differ in sign only:
+//  * pair sums and differences give drho = h_0 + sum (h_2p+1 + h_2p+2) and
+//    j = sum (h_2p+1 - h_2p+2) c_{2p+1};
+//  * a pair shares a = 4.5 (c.u)^2 - 1.5 u.u, and its two equilibria are
+//    w (drho + rho (a +- 3 c.u));
+//  * h' = (1 - omega) h + omega heq, with omega w rho and omega w drho formed
+//    once per weight class, is two fused multiply-adds per direction.
+// About 140 FP32 instructions a site against 210 for the direction-by-
+// direction form, in kernels whose 16-bit variants are issue-bound; emitting
+// each pair as soon as it is final lets a kernel store it and free its
+// registers.
+template <typename R, typename Emit>
+__device__ __forceinline__ void collide_emit(const R* h, R omega, Emit&& emit) {
+  R drho = h[0], jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const int i = 2 * p + 1;
+    const R sp = h[i] + h[i + 1], dp = h[i] - h[i + 1];
+    drho += sp;
+    if (cx(i)) jx = cx(i) > 0 ? jx + dp : jx - dp;
+    if (cy(i)) jy = cy(i) > 0 ? jy + dp : jy - dp;
+    if (cz(i)) jz = cz(i) > 0 ? jz + dp : jz - dp;
+  }
+  const R rho = R(1) + drho;
+  const R inv = R(1) / rho;
+  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  const R usq15 = R(1.5) * fmadd(uz, uz, fmadd(uy, uy, ux * ux));
+  const R om1 = R(1) - omega;
+  R wr[3], wd[3];  // omega w rho, omega w drho for w = 1/3, 1/18, 1/36
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const R ow = omega * wgt<R>(c == 0 ? 0 : (c == 1 ? 1 : 7));
+    wr[c] = ow * rho;
+    wd[c] = ow * drho;
+  }
+  emit(0, fmadd(om1, h[0], fmadd(-wr[0], usq15, wd[0])));
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const int i = 2 * p + 1, c = i <= 6 ? 1 : 2;
+    const R cu = cdotu<R>(i, ux, uy, uz);
+    const R a = fmadd(R(4.5) * cu, cu, -usq15);
+    emit(i, fmadd(om1, h[i], fmadd(wr[c], fmadd(R(3), cu, a), wd[c])));
+    emit(i + 1, fmadd(om1, h[i + 1], fmadd(wr[c], fmadd(R(-3), cu, a), wd[c])));
+  }
+}
+
+// The collision in place.
 template <typename R>
 __device__ __forceinline__ void collide(R* h, R omega) {
-  Macro<R> m = moments<R>(h);
-  R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+  R out[Q];
+  collide_emit<R>(h, omega, [&](int i, R v) { out[i] = v; });
 #pragma unroll
-  for (int i = 0; i < Q; ++i) h[i] += omega * (heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15) - h[i]);
+  for (int i = 0; i < Q; ++i) h[i] = out[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -232,21 +316,21 @@ __device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int
   for (int i = 1; i < Q; ++i) {
     const bool io = code[i] <= -2;
     const LinkRec L = links[io ? -code[i] - 2 : 0];       // record 0 exists whenever a site has an iolet link
-    const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+    const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
     if (!io) continue;
-    const IoletParam iop = p.io[L.iolet];
+    const IoletParam& iop = p.io[L.iolet];
     if (L.kind == 0) {
       R rho = p.ladd_rho_one ? R(1) : rho_s;
-      h[i] += R(L.coef) * rho * R(a) * R(io_val(p, L.iolet));
+      h[i] += BC<R>::coef(L) * rho * a * BC<R>::val(p, L.iolet);
     } else {
       R gx = ux, gy = uy, gz = uz;
       if (!p.ghost_full_u) {
-        R un = gx * R(iop.nx) + gy * R(iop.ny) + gz * R(iop.nz);
-        gx = un * R(iop.nx);
-        gy = un * R(iop.ny);
-        gz = un * R(iop.nz);
+        R un = gx * BC<R>::nx(iop) + gy * BC<R>::ny(iop) + gz * BC<R>::nz(iop);
+        gx = un * BC<R>::nx(iop);
+        gy = un * BC<R>::ny(iop);
+        gz = un * BC<R>::nz(iop);
       }
-      R drho = R(io_val(p, L.iolet));
+      R drho = BC<R>::val(p, L.iolet);
       R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
       h[i] = heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
     }
@@ -317,24 +401,57 @@ __device__ __forceinline__ Macro<R> lane_moments(R v) {
   m.uz = jz * inv;
   return m;
 }
+// collide() of a site held one direction per lane (lane i = direction i,
+// lanes 19..31 return 0), with the operations of collide_emit() in the same
+// order, so that a site gets the same bits whichever path steps it.
+template <typename R>
+__device__ __forceinline__ R lane_collide(R h, int i, R omega) {
+  R drho = __shfl_sync(FULL_MASK, h, 0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const int ip = 2 * p + 1;
+    const R a = __shfl_sync(FULL_MASK, h, ip), b = __shfl_sync(FULL_MASK, h, ip + 1);
+    const R sp = a + b, dp = a - b;
+    drho += sp;
+    if (cx(ip)) jx = cx(ip) > 0 ? jx + dp : jx - dp;
+    if (cy(ip)) jy = cy(ip) > 0 ? jy + dp : jy - dp;
+    if (cz(ip)) jz = cz(ip) > 0 ? jz + dp : jz - dp;
+  }
+  const R rho = R(1) + drho;
+  const R inv = R(1) / rho;
+  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
+  const R usq15 = R(1.5) * fmadd(uz, uz, fmadd(uy, uy, ux * ux));
+  const R om1 = R(1) - omega;
+  if (i >= Q) return R(0);
+  if (i == 0) {
+    const R ow = omega * wgt<R>(0);
+    return fmadd(om1, h, fmadd(-(ow * rho), usq15, ow * drho));
+  }
+  const int ip = 2 * ((i - 1) >> 1) + 1;
+  const R ow = omega * (ip <= 6 ? wgt<R>(1) : wgt<R>(7));
+  const R cu = lane_cdotu<R>(ip, ux, uy, uz);
+  const R a = fmadd(R(4.5) * cu, cu, -usq15);
+  return fmadd(om1, h, fmadd(ow * rho, fmadd((i & 1) ? R(3) : R(-3), cu, a), ow * drho));
+}
+
 // Boundary value of the lane's iolet link (as iolet_fixup computes it):
 // `out` = s'_ibar(x); rho_s, u_s the moments of the stored post-collision state.
 template <typename R>
-__device__ __forceinline__ R lane_iolet_value(int i, const LinkRec& L, R out, R rho_s, R ux, R uy, R uz, double a,
+__device__ __forceinline__ R lane_iolet_value(int i, const LinkRec& L, R out, R rho_s, R ux, R uy, R uz, R a,
                                               const StepParams& p) {
-  const IoletParam iop = p.io[L.iolet];
+  const IoletParam& iop = p.io[L.iolet];
   if (L.kind == 0) {
     R rho = p.ladd_rho_one ? R(1) : rho_s;
-    return out + R(L.coef) * rho * R(a) * R(io_val(p, L.iolet));
+    return out + BC<R>::coef(L) * rho * a * BC<R>::val(p, L.iolet);
   }
   R gx = ux, gy = uy, gz = uz;
   if (!p.ghost_full_u) {
-    R un = gx * R(iop.nx) + gy * R(iop.ny) + gz * R(iop.nz);
-    gx = un * R(iop.nx);
-    gy = un * R(iop.ny);
-    gz = un * R(iop.nz);
+    R un = gx * BC<R>::nx(iop) + gy * BC<R>::ny(iop) + gz * BC<R>::nz(iop);
+    gx = un * BC<R>::nx(iop);
+    gy = un * BC<R>::ny(iop);
+    gz = un * BC<R>::nz(iop);
   }
-  R drho = R(io_val(p, L.iolet));
+  R drho = BC<R>::val(p, L.iolet);
   R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
   return lane_heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
 }
@@ -446,6 +563,45 @@ __device__ __forceinline__ void load_codes(const int32_t* __restrict__ src, cons
   } else {
 #pragma unroll
     for (int i = 1; i < Q; ++i) s[i - 1] = ld_index<LD>(idx_at<WIDE>(src, i, sn, x));
+  }
+}
+
+// The 18 population offsets a bulk step kernel gathers from at site x (off[i],
+// i = 1..18): for a fluid source s the slot of row i at s (pull; AAODD: row
+// opp(i) at s), otherwise row opp(i) at x itself (AAODD: row i at x), which is
+// bounce-back (iolet links get their values elsewhere).  From the compact
+// table a link is fluid exactly when its offset is below CT_IOLET, so the
+// offset goes straight into the slot without forming a signed code.
+template <bool CT, bool WIDE, int LD, bool AAODD>
+__device__ __forceinline__ void load_offsets(const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
+                                             const int32_t* __restrict__ tbase, uint32_t sn, uint32_t n, uint32_t x,
+                                             uint32_t tile, uint32_t* off) {
+  if (CT) {
+    uint32_t w[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) w[q] = ld_index<LD>(WIDE ? ctab + ((uint64_t)q * sn + x) : ctab + (uint32_t)q * sn + x);
+    const int4* tb = reinterpret_cast<const int4*>(tbase + (uint64_t)tile * CT_BASES);
+    int b[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int4 v = __ldg(tb + q);
+      b[4 * q] = v.x;
+      b[4 * q + 1] = v.y;
+      b[4 * q + 2] = v.z;
+      b[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t o = (i & 1) ? (w[(i - 1) >> 1] & 0xffffu) : (w[(i - 1) >> 1] >> 16);
+      off[i] = o < CT_IOLET ? slot<WIDE>(AAODD ? opp(i) : i, n, (uint32_t)b[i - 1] + o)
+                            : slot<WIDE>(AAODD ? i : opp(i), n, x);
+    }
+  } else {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int32_t s = ld_index<LD>(idx_at<WIDE>(src, i, sn, x));
+      off[i] = s >= 0 ? slot<WIDE>(AAODD ? opp(i) : i, n, (uint32_t)s) : slot<WIDE>(AAODD ? i : opp(i), n, x);
+    }
   }
 }
 

@@ -91,9 +91,7 @@ __global__ void __launch_bounds__(BLOCK) k_step_local(const S* __restrict__ fin,
   R h[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) h[i] = ldpop(fin + (int64_t)i * n + x);
-  collide<R>(h, R(p.omega));
-#pragma unroll
-  for (int i = 0; i < Q; ++i) stpop<S>(fout + (int64_t)i * n + x, h[i]);
+  collide_emit<R>(h, omega_of<R>(p), [&](int i, R v) { stpop<S>(fout + (int64_t)i * n + x, v); });
 }
 
 // The same step for the sites with iolet links: one warp per site, lane i
@@ -122,15 +120,11 @@ __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __
   const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
   if (code <= -2) {
     const LinkRec L = links[-code - 2];
-    const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+    const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
     h = lane_iolet_value<R>(i, L, h, rho_s, ux, uy, uz, a, p);
   }
-  const Macro<R> m = lane_moments<R>(h);
-  const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-  if (dir) {
-    h += R(p.omega) * (lane_heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15) - h);
-    stpop<S>(fout + (int64_t)i * n + x, h);
-  }
+  h = lane_collide<R>(h, i, omega_of<R>(p));
+  if (dir) stpop<S>(fout + (int64_t)i * n + x, h);
 }
 
 // Pull A-B step from s'(t-1) in one launch: gather f(t) through the index
@@ -148,7 +142,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
                                                 const int32_t* __restrict__ tbase, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
                                                 int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
-                                                uint32_t pf, const StepParams p) {
+                                                const uint32_t* __restrict__ imask, uint32_t pf, const StepParams p) {
   using R = typename Real<S>::type;
   const unsigned b = blockIdx.x, j = b / stride;
   if (b % stride == 0 && j < n_iolet_blocks) {
@@ -160,20 +154,17 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
   const uint32_t x = tile * BLOCK + threadIdx.x;
   if (CT && pf && threadIdx.x < 32) prefetch_tile<S, sizeof(S) >= 4, false>(fin, ctab, tbase, n, sn, tile + pf);
   if (x >= n) return;
-  int32_t code[Q - 1];
-  load_codes<CT, WIDE, LD_STREAM>(src, ctab, tbase, sn, x, tile, code);
+  uint32_t off[Q];
+  load_offsets<CT, WIDE, LD_STREAM, false>(src, ctab, tbase, sn, n, x, tile, off);
+  // sites with an iolet link are stepped by the iolet warps (one 32-bit mask
+  // word per warp instead of a test of each of the 18 codes)
+  if ((__ldg(imask + (x >> 5)) >> (x & 31)) & 1u) return;
   R h[Q];
   h[0] = ldpop(fin + x);
-  bool iolet = false;
+  // fluid source: row i at s; otherwise row opp(i) at x (bounce-back)
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const int32_t s = code[i - 1];
-    // fluid source: row i at s; otherwise row opp(i) at x (bounce-back; iolets: step_iolet_site)
-    h[i] = ldpop(at<WIDE>(fin, i, n, s >= 0 ? slot<WIDE>(i, n, (uint32_t)s) : slot<WIDE>(opp(i), n, x)));
-    iolet |= s <= -2;
-  }
-  if (iolet) return;
-  collide<R>(h, R(p.omega));
+  for (int i = 1; i < Q; ++i) h[i] = ldpop(at<WIDE>(fin, i, n, off[i]));
+  collide<R>(h, omega_of<R>(p));
   if (WIDE) {
     stpop<S>(fout + x, h[0]);
 #pragma unroll
@@ -197,7 +188,7 @@ __global__ void __launch_bounds__(BLOCK) k_aa_even(S* A, const StepParams p) {
   R h[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) h[i] = to_real(A[(int64_t)i * n + x]);
-  collide<R>(h, R(p.omega));
+  collide<R>(h, omega_of<R>(p));
 #pragma unroll
   for (int i = 0; i < Q; ++i) stpop<S>(A + (int64_t)opp(i) * n + x, h[i]);
 }
@@ -281,7 +272,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_aa_even2(S* A, const StepParams p)
   float2 h[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) h[i] = P::to(A2[(int64_t)i * n2 + x2]);
-  collide2(h, float(p.omega));
+  collide2(h, p.omegaf);
 #pragma unroll
   for (int i = 0; i < Q; ++i) __stcs(A2 + (int64_t)opp(i) * n2 + x2, P::from(h[i].x, h[i].y));
 }
@@ -292,19 +283,19 @@ __global__ void __launch_bounds__(BLOCK, 4) k_aa_even2(S* A, const StepParams p)
 template <typename R>
 __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, R ux, R uy, R uz,
                                          const double* __restrict__ amp, const StepParams& p) {
-  const IoletParam io = p.io[L.iolet];
+  const IoletParam& io = p.io[L.iolet];
   if (L.kind == 0) {
     R r = p.ladd_rho_one ? R(1) : rho;
-    return out + R(L.coef) * r * R(amp[L.group]) * R(io_val(p, L.iolet));
+    return out + BC<R>::coef(L) * r * BC<R>::amp(p, amp, L.group) * BC<R>::val(p, L.iolet);
   }
   R gx = ux, gy = uy, gz = uz;
   if (!p.ghost_full_u) {
-    R un = gx * R(io.nx) + gy * R(io.ny) + gz * R(io.nz);
-    gx = un * R(io.nx);
-    gy = un * R(io.ny);
-    gz = un * R(io.nz);
+    R un = gx * BC<R>::nx(io) + gy * BC<R>::ny(io) + gz * BC<R>::nz(io);
+    gx = un * BC<R>::nx(io);
+    gy = un * BC<R>::ny(io);
+    gz = un * BC<R>::nz(io);
   }
-  R drho = R(io_val(p, L.iolet));
+  R drho = BC<R>::val(p, L.iolet);
   R usq15 = R(1.5) * (gx * gx + gy * gy + gz * gz);
   return heq<R>(i, drho, R(1) + drho, gx, gy, gz, usq15);
 }
@@ -354,7 +345,7 @@ __global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict_
   for (int i = 1; i < Q; ++i) {
     const bool io = code[i] <= -2;
     const LinkRec L = links[io ? -code[i] - 2 : 0];  // record 0 exists whenever a site has an iolet link
-    const double a = amp[L.kind == 0 && L.group >= 0 ? L.group : 0];
+    const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
     val[i] = io ? lane_iolet_value<R>(i, L, v[i], rho, ux, uy, uz, a, p) : R(0);
   }
 #pragma unroll
@@ -400,7 +391,7 @@ __global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int3
     off[i] = s >= 0 ? slot<WIDE>(opp(i), n, (uint32_t)s) : slot<WIDE>(i, n, x);
     h[i] = to_real(*at<WIDE>(A, i, n, off[i]));
   }
-  collide<R>(h, R(p.omega));
+  collide<R>(h, omega_of<R>(p));
   stpop<S>(A + x, h[0]);
 #pragma unroll
   for (int i = 1; i < Q; ++i) stpop<S>(at<WIDE>(A, i, n, off[i]), h[opp(i)]);
@@ -515,7 +506,7 @@ __global__ void __launch_bounds__(BLOCK) k_macros(const S* __restrict__ fin, con
     pxz += cx(i) * cz(i) * d;
     pyz += cy(i) * cz(i) * d;
   }
-  R k = -(R(1) - R(0.5) * R(p.omega));
+  R k = -(R(1) - R(0.5) * omega_of<R>(p));
   R tx = k * (pxx * nx + pxy * ny + pxz * nz);
   R ty = k * (pxy * nx + pyy * ny + pyz * nz);
   R tz = k * (pxz * nx + pyz * ny + pzz * nz);
@@ -695,7 +686,7 @@ struct StepOp {
       auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
                                : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
       kernel<<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase, h->d_links, h->d_amp,
-                                    h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1,
+                                    h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, h->d_imask,
                                     (uint32_t)h->n_sm * 5u, p);
     } else {
       k_step_local<S><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, p);
