@@ -9,16 +9,20 @@ synthetic and seeded; the paper's patient geometries are not available.
 One benchmark step = one LB time step over the whole lattice: one launch of
 the fused stream-collide-boundary kernel (pull A-B: k_step, iolet sites
 included), or for the AA pattern k_aa_odd / k_aa_even (alternating) plus
-the k_aa_fix pass over the iolet sites (0.2 % of the sites).  ``value`` is MLUPS (Eq. 9 of arXiv
-2202.11770) with the lattice resident in HBM; the state (~4.5 GB touched per
-step) is far larger than L2, so no flush is needed between steps.
+the k_aa_fix pass over the iolet sites (0.3 % of the sites).  ``value`` is MLUPS (Eq. 9 of arXiv
+2202.11770) with the lattice resident in HBM, timed with one CUDA event pair
+around all timed steps; the state (~3.4 GB touched per step) is far larger
+than L2, so no flush is needed between steps.
 
 ``--gpus N`` (under torchrun) runs N independent replicas, one per GPU
 (the single-GPU solver does not shard); ``value`` sums the ranks' site
 updates over the slowest rank's time.
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure, plain C,
-one thread) on the same lattice: a bounded number of full-lattice steps.
+sites split over all host cores) on the same lattice: a bounded number of
+full-lattice steps.  The default run also reports the oracle at one thread,
+and checks every storage form's velocity and wall shear stress against the
+oracle on a 1M-site tree after 1,000 steps (``precision_vs_oracle``).
 """
 from __future__ import annotations
 
@@ -75,12 +79,12 @@ CTYPE = {"fp32": "float", "bf16": "__nv_bfloat16", "fp16": "__half", "fp64": "do
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": "c4c6a1f8018e1f17",
-           # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, 20,000,864-site
+TRAFFIC = {"sha": "6aa4081d4c00a699",
+           # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (mean of two), 20,000,864-site
            # tree, kernels on the compact index table with the one-wave L2 prefetch
            "index": "compact",
-           "bytes_per_site": {"k_aa_odd": (2327549184 + 1475372032) / 20000864,
-                              "k_step": (2428723968 + 1485461504) / 20000864}}
+           "bytes_per_site": {"k_aa_odd": ((2346932224 + 1487981568) + (2347785728 + 1485053696)) / 2 / 20000864,
+                              "k_step": ((2466600704 + 1485242112) + (2451240960 + 1484932608)) / 2 / 20000864}}
 
 
 def kernel_sha() -> str:
@@ -178,28 +182,37 @@ def aggregate_ranks(ms_local, updates_local, dist=None, device="cpu"):
 
 
 def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55, wide=False, full_index=False):
-    """Time `steps` launches with a CUDA event after each (solver stream).
+    """Time `steps` steps on the solver stream, twice after `warmup` steps.
 
-    Returns (total_ms, per-step durations in ms, solver time before the
-    first timed step, whether the kernels read the compact index table)."""
+    The first pass has one CUDA event on each side of all steps (an event
+    recorded between steps costs ~5 us a step); it gives the total time.  The
+    second pass records an event after every step; it gives the duration of
+    each step kernel (AA: odd and even steps) for the roofline.  Returns
+    (total_ms, per-step durations in ms, solver time before the first
+    instrumented step, whether the kernels read the compact index table)."""
     from paper_2202_11770_gb300 import hemegb
     s = hemegb.Solver(lat, tau=tau, precision=precision, scheme=scheme, wide_offsets=wide, full_index=full_index)
     compact = s.compact_index
     set_bc(s, lat)
     s.init_equilibrium()
     s.step(warmup)
-    t_first = s.t
     stream = s.stream
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    t_first = s.t
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     ev[0].record(stream)
     for k in range(steps):
         s.step(1)
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
-    total = ev[0].elapsed_time(ev[-1])
     durs = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     mass, _ = s.reduce()
     assert math.isfinite(mass)
@@ -360,15 +373,86 @@ def precision_study(lat, checkpoints, torch):
     return out
 
 
-def cpu_baseline(lat, steps):
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_mlups(lat, steps, threads, tau=0.55, bc=None):
+    """FP64 oracle MLUPS over `steps` full-lattice steps after one warm-up step."""
     import oracle
-    o = oracle.Oracle(lat, tau=0.55)
-    set_bc(o, lat)
+    o = oracle.Oracle(lat, tau=tau, threads=threads)
+    if bc is None:
+        set_bc(o, lat)
+    else:
+        bc(o)
     o.init_equilibrium()
+    o.step(1)
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
     return lat.n * steps / dt / 1e6, dt
+
+
+def cpu_baseline(lat, steps_1, steps_all, pipe_steps):
+    """The FP64 oracle (test infrastructure, plain C) on the host cores: the
+    bench's tree at one thread and at all cores, and the 12,352-site pipe."""
+    from paper_2202_11770_gb300 import geometry
+    cores = host_cores()
+    v1, d1 = oracle_mlups(lat, steps_1, 1)
+    vn, dn = oracle_mlups(lat, steps_all, cores)
+    pipe = geometry.pipe(8.0, 64)
+
+    def pipe_bc(o):
+        o.set_velocity(0, [1.0], 0.01)
+        o.set_pressure(1, 1.0)
+    p1, pd1 = oracle_mlups(pipe, pipe_steps, 1, tau=0.8, bc=pipe_bc)
+    pn, pdn = oracle_mlups(pipe, pipe_steps, cores, tau=0.8, bc=pipe_bc)
+    return {"value": vn, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": (f"{steps_all} full-lattice steps of the {lat.n}-site tree on {cores} threads ({dn:.1f} s); "
+                       f"FP64 oracle, sites split over threads"),
+            "single_thread": {"value": v1, "sample": f"{steps_1} steps of the same tree ({d1:.1f} s)"},
+            "pipe_12352": {"threads_1": p1, f"threads_{cores}": pn, "steps": pipe_steps,
+                           "seconds": [round(pd1, 2), round(pdn, 2)]}}
+
+
+def precision_vs_oracle(sites, steps, torch, forms=(("fp32", "ab"), ("fp32", "aa"), ("bf16", "ab"), ("bf16", "aa"),
+                                                     ("fp16", "ab"), ("fp16", "aa"))):
+    """Velocity and wall-shear-stress error of each storage form against the
+    FP64 oracle: the seeded depth-6 tree at `sites` sites with the bench's
+    boundary conditions (pulsatile Ladd inlet, rho = 1 outlets, tau 0.55),
+    `steps` steps from rest, relative L2 over all sites (WSS over wall sites)."""
+    import oracle
+    from paper_2202_11770_gb300 import hemegb
+    lat = tree_lattice(sites)
+    cores = host_cores()
+    o = oracle.Oracle(lat, tau=0.55, threads=cores)
+    set_bc(o, lat)
+    o.init_equilibrium()
+    t0 = time.perf_counter()
+    o.step(steps)
+    t_oracle = time.perf_counter() - t0
+    _, u_o, wss_o = o.macros(lat.wall_normal)
+    del o
+    wall = ~np.isnan(wss_o)
+    out = {}
+    for prec, sch in forms:
+        s = hemegb.Solver(lat, tau=0.55, precision=prec, scheme=sch)
+        set_bc(s, lat)
+        s.init_equilibrium()
+        s.step(steps)
+        _, u, wss = s.macros()
+        out[f"{prec}_{sch}"] = {
+            "u_rel_l2": float(np.linalg.norm(u - u_o) / np.linalg.norm(u_o)),
+            "wss_rel_l2": float(np.linalg.norm(wss[wall] - wss_o[wall]) / np.linalg.norm(wss_o[wall]))}
+        del s
+    torch.cuda.empty_cache()
+    info = {"reference": "FP64 oracle", "workload": f"seeded depth-6 tree, {lat.n} sites, tau 0.55, pulsatile "
+            "Ladd inlet, 64 pressure outlets", "steps": steps, "oracle_threads": cores,
+            "oracle_s": round(t_oracle, 1)}
+    return out, info
 
 
 # ---------------------------------------------------------------------------
@@ -379,8 +463,9 @@ def run_reference(args):
     lat = tree_lattice(args.sites)
     w = min(args.warmup, 1)
     k = max(1, min(args.steps, args.ref_steps))
+    cores = host_cores()
     import oracle
-    o = oracle.Oracle(lat, tau=0.55)
+    o = oracle.Oracle(lat, tau=0.55, threads=cores)
     set_bc(o, lat)
     o.init_equilibrium()
     o.step(w)
@@ -388,13 +473,14 @@ def run_reference(args):
     o.step(k)
     dt = time.perf_counter() - t0
     v = lat.n * k / dt / 1e6
-    sample = f"{k} full-lattice steps of the {lat.n}-site tree after {w} warm-up step(s), FP64 oracle"
+    sample = (f"{k} full-lattice steps of the {lat.n}-site tree after {w} warm-up step(s), FP64 oracle "
+              f"on {cores} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": k, "warmup": w, "ms_per_step": dt / k * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_sites": lat.n},
-        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -457,11 +543,17 @@ def run_ours(args):
                "job": f"create + init + {args.e2e_steps} steps + host readback of rho,u every 100 steps",
                "create_s": round(t_create, 3), "total_s": round(t_all, 3)}
 
+    precision = None
+    if not args.quick and args.precision_sites > 0 and rank == 0:
+        errs, info = precision_vs_oracle(args.precision_sites, args.precision_steps, torch)
+        for key, e in errs.items():
+            if key in forms:
+                forms[key]["vs_oracle"] = e
+        precision = dict(info, forms=errs)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt = cpu_baseline(lat, args.cpu_steps)
-        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_steps} full-lattice steps of the {n}-site tree ({dt:.1f} s), FP64 oracle, 1 thread"}
+        cpu = cpu_baseline(lat, args.cpu_steps, args.cpu_steps_all, args.cpu_pipe_steps)
 
     if rank == 0:
         line = {
@@ -486,6 +578,7 @@ def run_ours(args):
             # per step: the fused kernel, plus the iolet fix-up pass for AA
             "gpu_launches": args.steps * (2 if scheme == "aa" and bool((lat.src <= -2).any()) else 1),
             "forms": forms,
+            "precision_vs_oracle": precision,
             "adjoint": adjoint,
         }
         print(json.dumps(line))
@@ -502,7 +595,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sites", type=int, default=20_000_000)
     ap.add_argument("--e2e-steps", type=int, default=2000)
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps of the one-thread CPU baseline")
+    ap.add_argument("--cpu-steps-all", type=int, default=6, help="oracle steps of the all-cores CPU baseline")
+    ap.add_argument("--cpu-pipe-steps", type=int, default=200, help="oracle steps on the 12,352-site pipe")
+    ap.add_argument("--precision-sites", type=int, default=1_000_000,
+                    help="tree size of the storage-precision check against the oracle (0: skip)")
+    ap.add_argument("--precision-steps", type=int, default=1000)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-sites", type=int, default=2_000_000)
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint/forward timing")

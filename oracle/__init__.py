@@ -50,6 +50,7 @@ def _load():
         lib.ora_free.argtypes = [_P]
         lib.ora_set_tau.argtypes = [_P, C.c_double]
         lib.ora_set_options.argtypes = [_P, C.c_int, C.c_int]
+        lib.ora_set_threads.argtypes = [_P, C.c_int]
         lib.ora_set_velocity.argtypes = [_P, C.c_int, _D, C.c_int, C.c_int, C.c_double, C.c_double,
                                          C.c_double, C.c_double, C.c_int, _D]
         lib.ora_set_pressure.argtypes = [_P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
@@ -120,7 +121,8 @@ def feq(rho: float, u) -> np.ndarray:
 class Oracle:
     """Plain FP64 LBGK solver on a sparse lattice (push streaming, AoS)."""
 
-    def __init__(self, lattice, tau: float, ladd_rho_one: bool = False, ghost_full_u: bool = False):
+    def __init__(self, lattice, tau: float, ladd_rho_one: bool = False, ghost_full_u: bool = False,
+                 threads: int = 1):
         lib = _load()
         self._lib = lib
         xyz = np.ascontiguousarray(lattice.xyz, dtype=np.int32)
@@ -147,6 +149,7 @@ class Oracle:
         self.tau = tau
         lib.ora_set_tau(h, float(tau))
         lib.ora_set_options(h, int(ladd_rho_one), int(ghost_full_u))
+        lib.ora_set_threads(h, int(threads))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -155,6 +158,12 @@ class Oracle:
             self._h = None
 
     # ---- parameters ----
+    def set_threads(self, threads: int):
+        """Host threads of a step (sites split into contiguous blocks).  The
+        state does not depend on the count; iolet fluxes are summed per block
+        and then in block order."""
+        self._lib.ora_set_threads(self._h, int(threads))
+
     def set_tau(self, tau: float):
         self.tau = tau
         self._lib.ora_set_tau(self._h, float(tau))

@@ -15,7 +15,7 @@ LIB = HERE / "liboracle.so"
 def build(force: bool = False) -> Path:
     if force or not LIB.exists() or LIB.stat().st_mtime < SRC.stat().st_mtime:
         tmp = LIB.with_suffix(".so.tmp")
-        r = subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-Wall",
+        r = subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-Wall",
                             "-o", str(tmp), str(SRC), "-lm"],
                            stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
         if r.returncode != 0:

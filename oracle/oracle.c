@@ -44,6 +44,7 @@
  *     resistance models as future work): see wk_t.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -137,6 +138,7 @@ typedef struct {
   int ladd_rho_one;  /* 1: use rho = 1 in the Ladd term instead of local rho */
   int ghost_full_u;  /* 1: ghost velocity = u instead of (u.n) n */
   double* flux;      /* [nio] mass entering through each iolet in the last step */
+  int threads;       /* host threads a step uses (1: serial) */
 } ora_t;
 
 /* ---------------- coordinate hash ---------------- */
@@ -262,6 +264,8 @@ int ora_create(int64_t n, const int32_t* xyz, const int32_t* src, int nio, const
 }
 
 void ora_set_tau(ora_t* o, double tau) { o->tau = tau; }
+/* Host threads of ora_step (default 1); the state is the same for any count. */
+void ora_set_threads(ora_t* o, int threads) { o->threads = threads > 1 ? threads : 1; }
 void ora_set_options(ora_t* o, int ladd_rho_one, int ghost_full_u) {
   o->ladd_rho_one = ladd_rho_one;
   o->ghost_full_u = ghost_full_u;
@@ -364,7 +368,57 @@ void ora_init_equilibrium(ora_t* o, double rho0, const double* u0) {
   }
 }
 
-/* One time step: collide every site, push to neighbours, apply BCs. */
+/* Collide site x and push its populations (with the boundary values of its
+ * wall and iolet links) into the next state; adds the mass each iolet link
+ * lets in to flux[k]. */
+static void site_step(ora_t* o, int64_t x, const double* wk, double* flux) {
+  const double* f = &o->f[x * Q];
+  double rho, u[3], feq[Q], fp[Q];
+  moments(f, &rho, u);
+  ora_feq(rho, u, feq);
+  const double omega = 1.0 / o->tau;
+  for (int i = 0; i < Q; ++i) fp[i] = f[i] - (f[i] - feq[i]) * omega;
+  for (int i = 0; i < Q; ++i) {
+    int32_t y = o->dest[x * Q + i];
+    if (y >= 0) {
+      o->fn[(int64_t)y * Q + i] = fp[i];
+      continue;
+    }
+    int ib = opposite(i);
+    double val;
+    if (y == -1) {
+      val = fp[i];
+    } else {
+      int k = -y - 2;
+      const iolet_t* io = &o->io[k];
+      if (io->kind == 0) {
+        double W = ladd_weight(io, &o->xyz[3 * x], i);
+        double A = o->amp[io->goff + o->group[x]] * wk[k];
+        double cu_w = A * W * (CV[i][0] * io->nrm[0] + CV[i][1] * io->nrm[1] + CV[i][2] * io->nrm[2]);
+        double r = o->ladd_rho_one ? 1.0 : rho;
+        val = fp[i] - 2.0 * weight(i) * r * cu_w / CS2;
+      } else {
+        double ug[3], geq[Q];
+        if (o->ghost_full_u) {
+          memcpy(ug, u, sizeof ug);
+        } else {
+          double un = u[0] * io->nrm[0] + u[1] * io->nrm[1] + u[2] * io->nrm[2];
+          for (int a = 0; a < 3; ++a) ug[a] = un * io->nrm[a];
+        }
+        ora_feq(wk[k], ug, geq);
+        val = geq[ib];
+      }
+      flux[k] += val - fp[i];
+    }
+    o->fn[x * Q + ib] = val;
+  }
+}
+
+/* One time step: collide every site, push to neighbours, apply BCs (Section
+ * 3.1).  Sites may be split over threads (ora_set_threads): every slot of the
+ * next state has exactly one writer, so the state does not depend on the
+ * thread count; each thread sums its own iolet fluxes over a contiguous block
+ * of sites and the blocks are added in thread order. */
 static void step_once(ora_t* o) {
   const int64_t n = o->n;
   const double t = (double)o->t;
@@ -377,49 +431,24 @@ static void step_once(ora_t* o) {
       wk[k] = wave_at(&o->io[k].wave, t);
     o->io[k].wk.rho_used = wk[k];
   }
-  for (int k = 0; k < o->nio; ++k) o->flux[k] = 0;
-  for (int64_t x = 0; x < n; ++x) {
-    const double* f = &o->f[x * Q];
-    double rho, u[3], feq[Q], fp[Q];
-    moments(f, &rho, u);
-    ora_feq(rho, u, feq);
-    const double omega = 1.0 / o->tau;
-    for (int i = 0; i < Q; ++i) fp[i] = f[i] - (f[i] - feq[i]) * omega;
-    for (int i = 0; i < Q; ++i) {
-      int32_t y = o->dest[x * Q + i];
-      if (y >= 0) {
-        o->fn[(int64_t)y * Q + i] = fp[i];
-        continue;
-      }
-      int ib = opposite(i);
-      double val;
-      if (y == -1) {
-        val = fp[i];
-      } else {
-        int k = -y - 2;
-        const iolet_t* io = &o->io[k];
-        if (io->kind == 0) {
-          double W = ladd_weight(io, &o->xyz[3 * x], i);
-          double A = o->amp[io->goff + o->group[x]] * wk[k];
-          double cu_w = A * W * (CV[i][0] * io->nrm[0] + CV[i][1] * io->nrm[1] + CV[i][2] * io->nrm[2]);
-          double r = o->ladd_rho_one ? 1.0 : rho;
-          val = fp[i] - 2.0 * weight(i) * r * cu_w / CS2;
-        } else {
-          double ug[3], geq[Q];
-          if (o->ghost_full_u) {
-            memcpy(ug, u, sizeof ug);
-          } else {
-            double un = u[0] * io->nrm[0] + u[1] * io->nrm[1] + u[2] * io->nrm[2];
-            for (int a = 0; a < 3; ++a) ug[a] = un * io->nrm[a];
-          }
-          ora_feq(wk[k], ug, geq);
-          val = geq[ib];
-        }
-        o->flux[k] += val - fp[i];
-      }
-      o->fn[x * Q + ib] = val;
+  const int nt = o->threads > 1 ? o->threads : 1;
+  const int nk = o->nio > 0 ? o->nio : 1;
+  double* part = (double*)calloc((size_t)nt * nk, sizeof(double));
+  if (nt == 1) {
+    for (int64_t x = 0; x < n; ++x) site_step(o, x, wk, part);
+  } else {
+#pragma omp parallel num_threads(nt)
+    {
+      const int tid = omp_get_thread_num(), cnt = omp_get_num_threads();
+      const int64_t b = n * tid / cnt, e = n * (tid + 1) / cnt;
+      for (int64_t x = b; x < e; ++x) site_step(o, x, wk, part + (size_t)tid * nk);
     }
   }
+  for (int k = 0; k < o->nio; ++k) {
+    o->flux[k] = 0;
+    for (int th = 0; th < nt; ++th) o->flux[k] += part[(size_t)th * nk + k];
+  }
+  free(part);
   double* tmp = o->f;
   o->f = o->fn;
   o->fn = tmp;

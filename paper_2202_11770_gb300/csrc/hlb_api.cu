@@ -467,10 +467,10 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
     e = cudaMemcpyAsync(h->d_red + nb, begin.data(), sizeof(int64_t) * begin.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nis > 0)
     e = cudaMemcpyAsync(h->d_iolet_sites, isites.data(), sizeof(int32_t) * (size_t)nis, cudaMemcpyHostToDevice, st);
-  // compact index codes of the iolet sites (the library's own re-coded table)
+  // index codes of the iolet sites (the library's own re-coded table), 18 per site
   std::vector<int32_t> icode((size_t)18 * (size_t)nis);
-  for (int i = 1; i < Q; ++i)
-    for (int64_t q = 0; q < nis; ++q) icode[(size_t)(i - 1) * nis + q] = src[(size_t)(i - 1) * sn + isites[q]];
+  for (int64_t q = 0; q < nis; ++q)
+    for (int i = 1; i < Q; ++i) icode[(size_t)q * 18 + (i - 1)] = src[(size_t)(i - 1) * sn + isites[q]];
   if (e == cudaSuccess && nis > 0)
     e = cudaMemcpyAsync(h->d_icode, icode.data(), sizeof(int32_t) * icode.size(), cudaMemcpyHostToDevice, st);
   // bit mask of the sites with an iolet link (bulk threads of k_step leave them to the iolet warps)

@@ -61,6 +61,16 @@ template <> __device__ __forceinline__ __half from_real<__half>(float v) { retur
 template <typename S> __device__ __forceinline__ S from_real(double v);
 template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
 
+// Programmatic dependent launch (sm_90 and later).  A step kernel lets the
+// next kernel of its stream be scheduled as soon as all of its own blocks are
+// resident (pdl_trigger), and waits for the previous kernel to complete, its
+// memory visible, before it reads anything that kernel wrote (pdl_wait).  The
+// next kernel's blocks then fill the SMs that the tail of this one frees,
+// instead of waiting for the launch after it ends.  Without the launch
+// attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Cached load of a population (read-only for the whole kernel).
 template <typename S>
 __device__ __forceinline__ typename Real<S>::type ldpop(const S* p) {

@@ -38,6 +38,24 @@ constexpr int BLOCK = 256;
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
+// Launch of a step-sequence kernel with programmatic stream serialisation
+// (pdl_trigger / pdl_wait in hlb_common.cuh): it may be scheduled while the
+// previous kernel of the stream finishes, and waits for it in pdl_wait.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // L2 prefetch hint: `bytes` (a multiple of 16) from a 16-byte aligned address.
 __device__ __forceinline__ void l2_prefetch(const void* q, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(q)), "r"(bytes)
@@ -87,6 +105,8 @@ __global__ void __launch_bounds__(BLOCK) k_step_local(const S* __restrict__ fin,
   using R = typename Real<S>::type;
   const int64_t n = p.n;
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (x >= n) return;
   R h[Q];
 #pragma unroll
@@ -146,6 +166,8 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
   using R = typename Real<S>::type;
   const unsigned b = blockIdx.x, j = b / stride;
   if (b % stride == 0 && j < n_iolet_blocks) {
+    pdl_wait();
+    pdl_trigger();
     step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
     return;
   }
@@ -153,12 +175,18 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
   const uint32_t tile = b - min(n_iolet_blocks, j + 1);
   const uint32_t x = tile * BLOCK + threadIdx.x;
   if (CT && pf && threadIdx.x < 32) prefetch_tile<S, sizeof(S) >= 4, false>(fin, ctab, tbase, n, sn, tile + pf);
-  if (x >= n) return;
   uint32_t off[Q];
-  load_offsets<CT, WIDE, LD_STREAM, false>(src, ctab, tbase, sn, n, x, tile, off);
+  const bool live = x < n;
   // sites with an iolet link are stepped by the iolet warps (one 32-bit mask
   // word per warp instead of a test of each of the 18 codes)
-  if ((__ldg(imask + (x >> 5)) >> (x & 31)) & 1u) return;
+  bool skip = true;
+  if (live) {
+    load_offsets<CT, WIDE, LD_STREAM, false>(src, ctab, tbase, sn, n, x, tile, off);
+    skip = (__ldg(imask + (x >> 5)) >> (x & 31)) & 1u;
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (skip) return;
   R h[Q];
   h[0] = ldpop(fin + x);
   // fluid source: row i at s; otherwise row opp(i) at x (bounce-back)
@@ -184,6 +212,8 @@ __global__ void __launch_bounds__(BLOCK) k_aa_even(S* A, const StepParams p) {
   using R = typename Real<S>::type;
   const int64_t n = p.n;
   const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (x >= n) return;
   R h[Q];
 #pragma unroll
@@ -266,6 +296,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_aa_even2(S* A, const StepParams p)
   using T = typename P::T;
   const int64_t n = p.n;
   const int64_t x = 2 * ((int64_t)blockIdx.x * BLOCK + threadIdx.x);
+  pdl_wait();
+  pdl_trigger();
   if (x >= n) return;
   T* A2 = reinterpret_cast<T*>(A);
   const int64_t n2 = n / 2, x2 = x / 2;
@@ -302,58 +334,46 @@ __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, 
 
 // After an AA step at time t: overwrite the slots that the iolet links of
 // each iolet site read in the next step with their boundary values, and
-// record the mass each link lets in.  One thread per iolet site: the whole
-// pass is one wave of threads, each with three rounds of independent loads
-// (index codes, stored populations, link records).  The site's stored
-// post-collision populations s'_ibar(x) sit in slot i of x after an even
-// step, and in the slot it read direction i from after an odd step; an iolet
-// link's slot is slot i of x in both cases.  Boundary values use the moments
-// of these stored values, as the A-B gather does.
-// icode[(i - 1) nsites + q] is the index code of direction i at iolet site
-// q, a compact copy of the table's rows (coalesced here, scattered there).
+// record the mass each link lets in.  One warp per iolet site, lane i =
+// direction i: its code, its stored value and (iolet link) its link record
+// are one load each, so the pass is three rounds of loads whatever the
+// site's number of iolet links.  The site's stored post-collision populations
+// s'_ibar(x) sit in slot i of x after an even step, and in the slot it read
+// direction i from after an odd step; an iolet link's slot is slot i of x in
+// both cases.  Boundary values use the moments of these stored values (summed
+// in direction order, as the per-thread read-back code does), as the A-B
+// gather does.  icode[q][i - 1] is the index code of direction i at iolet
+// site q: 72 contiguous bytes a site.
 template <typename S, bool ODD>
-__global__ void __launch_bounds__(128) k_aa_fix(S* A, const int32_t* __restrict__ icode,
+__global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict__ icode,
                                                 const LinkRec* __restrict__ links, const double* __restrict__ amp,
                                                 const int32_t* __restrict__ sites, int64_t nsites,
                                                 const StepParams p, double* __restrict__ lflux) {
   using R = typename Real<S>::type;
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nsites) return;
-  const int64_t n = p.n, x = sites[q];
-  int32_t code[Q];
-  code[0] = 0;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) code[i] = icode[(int64_t)(i - 1) * nsites + q];
-  R v[Q];  // v[i] = s'_ibar(x), the value in the slot the link of direction i reads
-#pragma unroll
-  for (int i = 0; i < Q; ++i)
-    v[i] = to_real(A[i == 0 ? x : (ODD ? aa_addr(i, code[i], n, x) : (int64_t)i * n + x)]);
-  R d = R(0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {  // rho = 1 + sum v, j = -sum v_k c_k, in direction order
-    d += v[k];
-    if (cx(k)) jx += cx(k) > 0 ? -v[k] : v[k];
-    if (cy(k)) jy += cy(k) > 0 ? -v[k] : v[k];
-    if (cz(k)) jz += cz(k) > 0 ? -v[k] : v[k];
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int i = threadIdx.x & 31;
+  int64_t x = 0;
+  int32_t code = 0;
+  if (q < nsites) {
+    x = __ldg(sites + q);
+    if (i >= 1 && i < Q) code = __ldg(icode + q * (Q - 1) + (i - 1));
   }
+  pdl_wait();
+  pdl_trigger();
+  if (q >= nsites) return;  // uniform across the warp
+  const int64_t n = p.n;
+  R v = R(0);  // s'_ibar(x), the value in the slot the link of direction i reads
+  if (i < Q) v = to_real(A[i == 0 ? x : (ODD ? aa_addr(i, code, n, x) : (int64_t)i * n + x)]);
+  R d, jx, jy, jz;  // rho = 1 + sum v, j = -sum v_k c_k, in direction order
+  lane_moment_sums<R>(v, R(-1), &d, &jx, &jy, &jz);
   const R rho = R(1) + d;
   const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
-  // all loads first, stores after: the record and amplitude loads of the 18
-  // directions can then be in flight together
-  R val[Q];
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const bool io = code[i] <= -2;
-    const LinkRec L = links[io ? -code[i] - 2 : 0];  // record 0 exists whenever a site has an iolet link
-    const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
-    val[i] = io ? lane_iolet_value<R>(i, L, v[i], rho, ux, uy, uz, a, p) : R(0);
-  }
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    if (code[i] > -2) continue;
-    lflux[-code[i] - 2] = (double)val[i] - (double)v[i];
-    A[(int64_t)i * n + x] = from_real<S>(val[i]);
-  }
+  if (code > -2) return;
+  const LinkRec L = links[-code - 2];
+  const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
+  const R val = lane_iolet_value<R>(i, L, v, rho, ux, uy, uz, a, p);
+  lflux[-code - 2] = (double)val - (double)v;
+  A[(int64_t)i * n + x] = from_real<S>(val);
 }
 
 // Odd step: gather f(t) through the index table, collide, and write each
@@ -378,9 +398,11 @@ __global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int3
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
   const uint32_t x = blockIdx.x * BLOCK + threadIdx.x;
   if (CT && pf && threadIdx.x < 32) prefetch_tile<S, sizeof(S) >= 4, true>(A, ctab, tbase, n, sn, blockIdx.x + pf);
-  if (x >= n) return;
   int32_t code[Q - 1];
-  load_codes<CT, WIDE, LD_NC>(src, ctab, tbase, sn, x, blockIdx.x, code);
+  if (x < n) load_codes<CT, WIDE, LD_NC>(src, ctab, tbase, sn, x, blockIdx.x, code);
+  pdl_wait();
+  pdl_trigger();
+  if (x >= n) return;
   uint32_t off[Q];
   R h[Q];
   h[0] = to_real(A[x]);
@@ -685,56 +707,48 @@ struct StepOp {
       const unsigned grid = gi + grid_for(h->n);
       auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
                                : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
-      kernel<<<grid, BLOCK, 0, s>>>((const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase, h->d_links, h->d_amp,
-                                    h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, h->d_imask,
-                                    (uint32_t)h->n_sm * 5u, p);
-    } else {
-      k_step_local<S><<<grid_for(h->n), BLOCK, 0, s>>>((const S*)fin, (S*)fout, p);
+      return launch_pdl(kernel, grid, BLOCK, s, (const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase,
+                        h->d_links, h->d_amp, h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, h->d_imask,
+                        (uint32_t)h->n_sm * 5u, p);
     }
-    return cudaGetLastError();
+    return launch_pdl(k_step_local<S>, grid_for(h->n), BLOCK, s, (const S*)fin, (S*)fout, p);
   }
 };
 
 template <typename S>
-void aa_even(const hlb_solver* h, S* A, const StepParams& p, cudaStream_t s) {
-  k_aa_even<S><<<grid_for(h->n), BLOCK, 0, s>>>(A, p);
+cudaError_t aa_even(const hlb_solver* h, S* A, const StepParams& p, cudaStream_t s) {
+  return launch_pdl(k_aa_even<S>, grid_for(h->n), BLOCK, s, A, p);
+}
+template <typename S>
+cudaError_t aa_even_pairs(const hlb_solver* h, S* A, const StepParams& p, cudaStream_t s) {
+  if (h->n % 2 == 0) return launch_pdl(k_aa_even2<S>, grid_for(h->n / 2), BLOCK, s, A, p);
+  return launch_pdl(k_aa_even<S>, grid_for(h->n), BLOCK, s, A, p);
 }
 template <>
-void aa_even<__nv_bfloat16>(const hlb_solver* h, __nv_bfloat16* A, const StepParams& p, cudaStream_t s) {
-  if (h->n % 2 == 0)
-    k_aa_even2<__nv_bfloat16><<<grid_for(h->n / 2), BLOCK, 0, s>>>(A, p);
-  else
-    k_aa_even<__nv_bfloat16><<<grid_for(h->n), BLOCK, 0, s>>>(A, p);
+cudaError_t aa_even<__nv_bfloat16>(const hlb_solver* h, __nv_bfloat16* A, const StepParams& p, cudaStream_t s) {
+  return aa_even_pairs<__nv_bfloat16>(h, A, p, s);
 }
 template <>
-void aa_even<__half>(const hlb_solver* h, __half* A, const StepParams& p, cudaStream_t s) {
-  if (h->n % 2 == 0)
-    k_aa_even2<__half><<<grid_for(h->n / 2), BLOCK, 0, s>>>(A, p);
-  else
-    k_aa_even<__half><<<grid_for(h->n), BLOCK, 0, s>>>(A, p);
+cudaError_t aa_even<__half>(const hlb_solver* h, __half* A, const StepParams& p, cudaStream_t s) {
+  return aa_even_pairs<__half>(h, A, p, s);
 }
 
 template <typename S>
 struct AAOp {
   static cudaError_t run(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
     StepParams p = h->params(t);
+    cudaError_t e;
     if (odd)
-      (h->compact ? (h->off32 ? k_aa_odd<S, false, true> : k_aa_odd<S, true, true>)
-                  : (h->off32 ? k_aa_odd<S, false, false> : k_aa_odd<S, true, false>))
-          <<<grid_for(h->n), BLOCK, 0, s>>>((S*)A, h->d_src, h->d_ctab, h->d_tbase,
-                                            (uint32_t)h->n_sm * (h->off32 ? 5u : 4u), p);
+      e = launch_pdl(h->compact ? (h->off32 ? k_aa_odd<S, false, true> : k_aa_odd<S, true, true>)
+                                : (h->off32 ? k_aa_odd<S, false, false> : k_aa_odd<S, true, false>),
+                     grid_for(h->n), BLOCK, s, (S*)A, h->d_src, h->d_ctab, h->d_tbase,
+                     (uint32_t)h->n_sm * (h->off32 ? 5u : 4u), p);
     else
-      aa_even<S>(h, (S*)A, p, s);
-    if (h->n_iolet_sites > 0) {
-      const unsigned g = (unsigned)((h->n_iolet_sites + 127) / 128);  // one thread per iolet site
-      if (odd)
-        k_aa_fix<S, true><<<g, 128, 0, s>>>((S*)A, h->d_icode, h->d_links, h->d_amp, h->d_iolet_sites,
-                                            h->n_iolet_sites, p, h->d_lflux);
-      else
-        k_aa_fix<S, false><<<g, 128, 0, s>>>((S*)A, h->d_icode, h->d_links, h->d_amp, h->d_iolet_sites,
-                                             h->n_iolet_sites, p, h->d_lflux);
-    }
-    return cudaGetLastError();
+      e = aa_even<S>(h, (S*)A, p, s);
+    if (e != cudaSuccess || h->n_iolet_sites == 0) return e;
+    const unsigned g = (unsigned)((h->n_iolet_sites + 7) / 8);  // one warp per iolet site
+    return launch_pdl(odd ? k_aa_fix<S, true> : k_aa_fix<S, false>, g, 256, s, (S*)A, h->d_icode, h->d_links,
+                      h->d_amp, h->d_iolet_sites, h->n_iolet_sites, p, h->d_lflux);
   }
 };
 
@@ -818,6 +832,8 @@ __global__ void __launch_bounds__(BLOCK) k_wk_update(const S* __restrict__ fin, 
   using R = typename Real<S>::type;
   __shared__ double sh[BLOCK / 32];
   const int k = blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (!((p.coupled[k >> 6] >> (k & 63)) & 1ull)) return;  // uniform per block
   if (!AA && shift) {
     if (threadIdx.x == 0) ioval[k] = iovnext[k];
@@ -881,14 +897,11 @@ struct WkOp {
     const int64_t nb = grid_for(h->n);
     const int64_t* begin = (const int64_t*)(h->d_red + nb);  // link ranges stored after the reduction partials
     if (h->scheme == HLB_AA)
-      k_wk_update<S, true><<<(unsigned)h->n_iolets, BLOCK, 0, s>>>(nullptr, h->d_links, h->d_amp, p, begin,
-                                                                   h->d_lflux, h->d_wkpar, h->d_wkstate,
-                                                                   h->d_ioval, h->d_iovnext, 0);
-    else
-      k_wk_update<S, false><<<(unsigned)h->n_iolets, BLOCK, 0, s>>>((const S*)fin, h->d_links, h->d_amp, p,
-                                                                    begin, nullptr, h->d_wkpar, h->d_wkstate,
-                                                                    h->d_ioval, h->d_iovnext, shift ? 1 : 0);
-    return cudaGetLastError();
+      return launch_pdl(k_wk_update<S, true>, (unsigned)h->n_iolets, BLOCK, s, (const S*)nullptr, h->d_links,
+                        h->d_amp, p, begin, h->d_lflux, h->d_wkpar, h->d_wkstate, h->d_ioval, h->d_iovnext, 0);
+    return launch_pdl(k_wk_update<S, false>, (unsigned)h->n_iolets, BLOCK, s, (const S*)fin, h->d_links, h->d_amp,
+                      p, begin, (const double*)nullptr, h->d_wkpar, h->d_wkstate, h->d_ioval, h->d_iovnext,
+                      shift ? 1 : 0);
   }
 };
 

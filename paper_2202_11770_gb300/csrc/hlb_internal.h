@@ -69,7 +69,7 @@ struct hlb_solver {
   double* d_red = nullptr;            // reduction scratch
   double* d_lflux = nullptr;          // [n_links] mass let in by each iolet link in the last AA step
   int32_t* d_iolet_sites = nullptr;   // sites with at least one iolet link (AA boundary fix-up)
-  int32_t* d_icode = nullptr;         // [18][n_iolet_sites] their index codes, compact
+  int32_t* d_icode = nullptr;         // [n_iolet_sites][18] their index codes
   uint32_t* d_imask = nullptr;        // [(n + 31) / 32] bit x % 32 of word x / 32: site x has an iolet link
   int64_t* d_ioff = nullptr;          // [n_iolets + 1] ranges of d_ilist per iolet
   int32_t* d_ilist = nullptr;         // sites with a link to iolet k, ascending, iolet by iolet

@@ -37,8 +37,8 @@ MUTANTS = [
      "val = fp[i] - weight(i) * r * cu_w / CS2;", LADD),
     ("Ladd correction over cs^4", "val = fp[i] - 2.0 * weight(i) * r * cu_w / CS2;",
      "val = fp[i] - 2.0 * weight(i) * r * cu_w / (CS2 * CS2);", LADD),
-    ("Ladd density fixed at 1", "double r = o->ladd_rho_one ? 1.0 : rho;\n          val = fp[i]",
-     "double r = 1.0;\n          val = fp[i]", LADD),
+    ("Ladd density fixed at 1", "double r = o->ladd_rho_one ? 1.0 : rho;\n        val = fp[i]",
+     "double r = 1.0;\n        val = fp[i]", LADD),
     ("Ladd weight at the site, not the link midpoint", "m[a] = p[a] + 0.5 * CV[i][a];", "m[a] = p[a];", LADD),
     ("Ladd weight with the diameter as radius", "r2 / (io->R * io->R)", "r2 / (4.0 * io->R * io->R)", LADD),
     ("Ladd correction without the factor 2 (flow pins)", "val = fp[i] - 2.0 * weight(i) * r * cu_w / CS2;",
@@ -54,7 +54,7 @@ MUTANTS = [
 def _build(text, path):
     path.write_text(text)
     lib = path.with_suffix(".so")
-    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-o", str(lib), str(path), "-lm"],
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-o", str(lib), str(path), "-lm"],
                    check=True, capture_output=True)
     return lib
 
