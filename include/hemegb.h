@@ -108,8 +108,9 @@ typedef struct {
 /* precision: HLB_FP32 / HLB_BF16 / HLB_FP16 / HLB_FP64 storage.
  * scheme: HLB_PULL_AB (two population buffers, pull gather) or HLB_AA
  *   (one buffer, alternating in-place even/odd steps); AUTO picks the
- *   scheme measured faster for the lattice size: pull A-B below 4M sites
- *   (one launch per step), AA from 4M sites on (fewer bytes per site).
+ *   scheme measured faster for the lattice size: pull A-B below 750k sites
+ *   (one launch per step; such states fit in the GPU's L2 cache), AA from
+ *   750k sites on (fewer bytes per site).
  * ladd_rho_one: 1 = use rho = 1 in the Ladd correction instead of the
  *   site's density (the paper does not say which density).
  * ghost_full_u: 1 = pressure-iolet ghost velocity u instead of (u.n) n.
@@ -283,13 +284,21 @@ int hlb_n_amp_groups(const hlb_solver* h);
  * acceptable.  Sums a shifted population array f [19][n_sites] (device
  * memory, storage `precision`, e.g. written by hlb_get_state with
  * HLB_DEVICE) into *mass (one double in device memory) as
- * n_sites + sum of all entries, in FP64, asynchronously on `stream`; the
- * result equals hlb_reduce's mass of the same state.  Its per-block partial
+ * n_sites + sum of all entries, in FP64, asynchronously on `stream`.  For
+ * FP32 and FP64 storage, and for AA-scheme states in any precision, the
+ * result equals hlb_reduce's mass of the same state.  A 16-bit state that
+ * hlb_get_state reads back after a pull A-B step carries the boundary values
+ * of the iolet links rounded to the storage format, which hlb_reduce sums
+ * unrounded: the two masses then differ by at most the sum of half an ulp of
+ * each of those values.  Its per-block partial
  * sums live in a fixed 2 MiB device array inside the library (one copy per
  * GPU that loads the library, held until the process exits), so n_sites may
  * not exceed HLB_STATIC_MAX_SITES: larger sizes return HLB_ERR_ARG.  The
  * first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  Every
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture.  cudaDeviceReset ends the device's context
+ * and with it that address: do not call this entry point on a device after
+ * resetting it.  Every
  * call shares the array and leaves its partial sums there; nothing in it
  * needs to start at zero.  Calls that overlap on the GPU (two streams, or two
  * host threads) race on it and must be serialised by the caller.  No

@@ -15,15 +15,14 @@
 // G_t^T is itself a gather: s'_i(x) is read by the site x + c_i, whose
 // index is src[opp(i)][x], or (boundary link) by x itself in direction
 // opp(i).  One kernel per reverse step reads the index table and gathers
-// both mu(t+1) and s'(t-1) (to recompute f(t)).  J itself is summed in the
-// reverse sweep too, where f(t)'s moments are at hand, so the forward sweep
-// runs the plain step kernels of the solver's scheme and nothing else.  The
-// reverse kernel reads the int32 index table: with the compact table (whose
-// decoding needs more registers) it spilled at four blocks per SM and
-// measured slower.
+// both mu(t+1) and s'(t-1) (to recompute f(t)), from one decode of the
+// index (the compact table when the lattice fits it).  J itself is summed in
+// the reverse sweep too, where f(t)'s moments are at hand, so the forward
+// sweep runs the plain step kernels of the solver's scheme and nothing else.
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "hlb_internal.h"
@@ -46,7 +45,17 @@ struct ProbeMap {
   double* jp;            // per-probe objective accumulators, ordered by site
   double ax, ay, az;
   double inv_n;          // 1 / N
+  float axf, ayf, azf;   // the axis rounded to float on the host (FP32 kernels)
 };
+
+// The probe axis in the arithmetic type of a kernel.
+template <typename R> __device__ __forceinline__ void probe_axis(const ProbeMap& pm, R* a);
+template <> __device__ __forceinline__ void probe_axis<float>(const ProbeMap& pm, float* a) {
+  a[0] = pm.axf; a[1] = pm.ayf; a[2] = pm.azf;
+}
+template <> __device__ __forceinline__ void probe_axis<double>(const ProbeMap& pm, double* a) {
+  a[0] = pm.ax; a[1] = pm.ay; a[2] = pm.az;
+}
 
 // At a probe, with d = u(t).axis - target: J gains d^2 / N (when add_j) and
 // dJ/df_j(t) = pg (c_j . axis - u_ax) with pg = 2 d / (N rho).  pg = 0 off
@@ -83,87 +92,192 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;
 }
 
+// Sum over a block in the arithmetic type R (fixed order): warp xor
+// butterflies, then thread 0 adds the warps' sums in order.  Valid in thread 0.
+template <typename R>
+__device__ __forceinline__ R block_sum_r(R v, R* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  R r = R(0);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+  return r;
+}
+
+// Offsets of the two gathers of a reverse step at site x.  off[i] is the
+// slot f_i(x, t) is gathered from: row i at the fluid source s = x - c_i, or
+// row opp(i) at x itself (boundary link); bit i of *fluid says which.  The
+// adjoint gather of mu(t+1) reads, for direction i, row opp(i) at s (fluid)
+// or row i at x: in both offset forms that is off[i] + n when the link is
+// fluid and i is odd or the link is not fluid and i is even, and off[i] - n
+// otherwise (mu_offset), so one decode of the index serves both gathers.
+template <bool CT, bool WIDE>
+__device__ __forceinline__ void reverse_offsets(const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
+                                                const int32_t* __restrict__ tbase, uint32_t sn, uint32_t n,
+                                                uint32_t x, uint32_t tile, uint32_t* off, uint32_t* fluid) {
+  uint32_t fl = 0;
+  if (CT) {
+    uint32_t w[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) w[q] = __ldg(WIDE ? ctab + ((uint64_t)q * sn + x) : ctab + (uint32_t)q * sn + x);
+    const int4* tb = reinterpret_cast<const int4*>(tbase + (uint64_t)tile * CT_BASES);
+    int b[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int4 v = __ldg(tb + q);
+      b[4 * q] = v.x;
+      b[4 * q + 1] = v.y;
+      b[4 * q + 2] = v.z;
+      b[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t o = (i & 1) ? (w[(i - 1) >> 1] & 0xffffu) : (w[(i - 1) >> 1] >> 16);
+      const bool f = o < CT_IOLET;
+      off[i] = f ? slot<WIDE>(i, n, (uint32_t)b[i - 1] + o) : slot<WIDE>(opp(i), n, x);
+      fl |= f ? 1u << i : 0u;
+    }
+  } else {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int32_t s = __ldg(idx_at<WIDE>(src, i, sn, x));
+      off[i] = s >= 0 ? slot<WIDE>(i, n, (uint32_t)s) : slot<WIDE>(opp(i), n, x);
+      fl |= s >= 0 ? 1u << i : 0u;
+    }
+  }
+  *fluid = fl;
+}
+__device__ __forceinline__ uint32_t mu_offset(uint32_t off, uint32_t fluid, int i, uint32_t n) {
+  return (((fluid >> i) & 1u) == (uint32_t)(i & 1)) ? off + n : off - n;
+}
+
 // Bulk reverse step over all sites without iolet links, one site per
-// thread.  f(t) is gathered from s'(t-1) first; its moments are kept and its
-// non-equilibrium parts h_i - heq_i are parked in shared memory, so that the
-// 19 gathered values of mu(t+1) can reuse the registers.  Then
-// lam = G_t^T mu(t+1) and mu_j(t) = (1 - omega) lam_j + omega (S0 + (c_j - u).B)
-// plus the probe term.  The index row is read twice (once per gather); the
-// second read hits L1.  Staging the index rows in shared memory with bulk
-// copies measured no faster here and costs 56 KiB of shared memory per
-// block; issuing both gathers together (no parked parts, 3 or 2 blocks per
-// SM) measured slower.
-template <typename S, bool GPREV, bool WIDE>
-__device__ __forceinline__ double adjoint_site(const S* __restrict__ prev, const S* __restrict__ mu_next,
-                                               S* __restrict__ mu_out, const int32_t* __restrict__ src,
-                                               const AdjParams& ap, const ProbeMap& pm, int store, int64_t x,
-                                               typename Real<S>::type (*neq)[BLOCK]) {
+// thread.  f(t) is gathered from s'(t-1) first (GPREV; otherwise it is read
+// in place from a checkpoint); its moments are kept and its non-equilibrium
+// parts h_i - heq_i are parked in shared memory, so that the 19 gathered
+// values of mu(t+1) can reuse the registers.  Then lam = G_t^T mu(t+1) and
+// mu_j(t) = (1 - omega) lam_j + omega (S0 + (c_j - u).B) plus the probe term,
+// with S0 = sum lam_i feq_i / rho, B = sum lam_i w_i (3 + 9 c_i.u) c_i - 3 u L,
+// L = sum lam_i w_i.  Like the forward collision, the sums run over opposite
+// pairs, whose c.u differ in sign only: a pair adds w (s (1 + a) + 3 c.u d) to
+// S0, w s to L and w (3 d + 9 c.u s) c to B, with s and d the pair's sum and
+// difference of lam.  The index is decoded once for both gathers
+// (reverse_offsets).  Measured and dropped: both gathers issued at once as
+// asynchronous copies into shared memory (5 instead of 4 blocks per SM, no
+// faster), both gathers in registers (no parked parts, 3 or 2 blocks per SM),
+// and the index rows staged in shared memory with bulk copies.
+template <typename S, bool GPREV, bool WIDE, bool CT>
+__device__ __forceinline__ typename Real<S>::type adjoint_site(const S* __restrict__ prev, const S* __restrict__ mu_next,
+                                                               S* __restrict__ mu_out, const int32_t* __restrict__ src,
+                                                               const uint32_t* __restrict__ ctab,
+                                                               const int32_t* __restrict__ tbase,
+                                                               const uint32_t* __restrict__ imask,
+                                                               const AdjParams& ap, const ProbeMap& pm, int store,
+                                                               int64_t x, uint32_t tile,
+                                                               typename Real<S>::type (*neq)[BLOCK]) {
   using R = typename Real<S>::type;
   const uint32_t n = (uint32_t)ap.prev.n, sn = (uint32_t)ap.prev.sn, xi = (uint32_t)x;
   const R omega = omega_of<R>(ap.prev);
-  double dtau_local = 0;
-  bool iolet = x >= ap.prev.n;
-  Macro<R> m;
-  if (!iolet) {
+  if (x >= ap.prev.n) return R(0);
+  if ((__ldg(imask + (xi >> 5)) >> (xi & 31)) & 1u) return R(0);  // iolet sites: adjoint_iolet_site
+  uint32_t off[Q], fluid;
+  reverse_offsets<CT, WIDE>(src, ctab, tbase, sn, n, xi, tile, off, &fluid);
+  R drho, rho, ux, uy, uz, usq15;
+  {
     R h[Q];
     h[0] = ldpop(prev + xi);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int32_t s = __ldg(idx_at<WIDE>(src, i, sn, xi));
-      h[i] = ldpop(at<WIDE>(prev, i, n,
-                            GPREV ? (s >= 0 ? slot<WIDE>(i, n, (uint32_t)s) : slot<WIDE>(opp(i), n, xi))
-                                  : slot<WIDE>(i, n, xi)));
-      iolet |= s <= -2;
-    }
-    if (!iolet) {  // iolet sites: adjoint_iolet_site
-      m = moments<R>(h);
-      const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
+    for (int i = 1; i < Q; ++i) h[i] = ldpop(at<WIDE>(prev, i, n, GPREV ? off[i] : slot<WIDE>(i, n, xi)));
+    drho = h[0];
+    R jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) neq[i][threadIdx.x] = h[i] - heq<R>(i, m.drho, m.rho, m.ux, m.uy, m.uz, usq15);
+    for (int p = 0; p < 9; ++p) {
+      const int i = 2 * p + 1;
+      const R dp = h[i] - h[i + 1];
+      drho += h[i] + h[i + 1];
+      if (cx(i)) jx = cx(i) > 0 ? jx + dp : jx - dp;
+      if (cy(i)) jy = cy(i) > 0 ? jy + dp : jy - dp;
+      if (cz(i)) jz = cz(i) > 0 ? jz + dp : jz - dp;
+    }
+    rho = R(1) + drho;
+    const R inv = R(1) / rho;
+    ux = jx * inv;
+    uy = jy * inv;
+    uz = jz * inv;
+    usq15 = R(1.5) * fmadd(uz, uz, fmadd(uy, uy, ux * ux));
+    neq[0][threadIdx.x] = h[0] - wgt<R>(0) * fmadd(-rho, usq15, drho);
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+      const int i = 2 * p + 1;
+      const R w = wgt<R>(i), cu = cdotu<R>(i, ux, uy, uz);
+      const R a = fmadd(R(4.5) * cu, cu, -usq15);
+      neq[i][threadIdx.x] = h[i] - w * fmadd(rho, fmadd(R(3), cu, a), drho);
+      neq[i + 1][threadIdx.x] = h[i + 1] - w * fmadd(rho, fmadd(R(-3), cu, a), drho);
     }
   }
-  if (!iolet) {
-    R lam[Q];
-    lam[0] = ldpop(mu_next + xi);
+  R lam[Q];
+  lam[0] = ldpop(mu_next + xi);
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int32_t s = __ldca(idx_at<WIDE>(src, i, sn, xi));  // a re-read, not held in registers
-      // s'_opp(i)(x) is read by x - c_i = x + c_opp(i) in direction opp(i)
-      lam[opp(i)] = ldpop(at<WIDE>(mu_next, i, n, s >= 0 ? slot<WIDE>(opp(i), n, (uint32_t)s) : slot<WIDE>(i, n, xi)));
+  for (int i = 1; i < Q; ++i) lam[opp(i)] = ldpop(at<WIDE>(mu_next, i, n, mu_offset(off[i], fluid, i, n)));
+  // sums per weight class (1: axis pairs, 2: diagonal pairs)
+  R S1 = R(0), S2 = R(0), L1 = R(0), L2 = R(0), B1x = R(0), B1y = R(0), B1z = R(0), B2x = R(0), B2y = R(0),
+    B2z = R(0), dt = lam[0] * neq[0][threadIdx.x];
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const int i = 2 * p + 1;
+    const R sp = lam[i] + lam[i + 1], dp = lam[i] - lam[i + 1];
+    const R cu = cdotu<R>(i, ux, uy, uz);
+    const R a = fmadd(R(4.5) * cu, cu, -usq15);
+    const R sv = fmadd(R(3) * cu, dp, sp * (R(1) + a));
+    const R q = fmadd(R(9) * cu, sp, R(3) * dp);
+    dt = fmadd(lam[i], neq[i][threadIdx.x], dt);
+    dt = fmadd(lam[i + 1], neq[i + 1][threadIdx.x], dt);
+    if (i <= 6) {
+      S1 += sv;
+      L1 += sp;
+      if (cx(i)) B1x += cx(i) > 0 ? q : -q;
+      if (cy(i)) B1y += cy(i) > 0 ? q : -q;
+      if (cz(i)) B1z += cz(i) > 0 ? q : -q;
+    } else {
+      S2 += sv;
+      L2 += sp;
+      if (cx(i)) B2x += cx(i) > 0 ? q : -q;
+      if (cy(i)) B2y += cy(i) > 0 ? q : -q;
+      if (cz(i)) B2z += cz(i) > 0 ? q : -q;
     }
-    const R usq15 = R(1.5) * (m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-    R S0 = R(0), Lw = R(0), Bx = R(0), By = R(0), Bz = R(0), dt = R(0);
+  }
+  const R w0 = wgt<R>(0), w1 = wgt<R>(1), w2 = wgt<R>(7);
+  const R S0 = fmadd(w0 * lam[0], R(1) - usq15, fmadd(w1, S1, w2 * S2));
+  const R Lw = fmadd(w0, lam[0], fmadd(w1, L1, w2 * L2));
+  const R Bx = fmadd(w1, B1x, w2 * B2x) - R(3) * ux * Lw;
+  const R By = fmadd(w1, B1y, w2 * B2y) - R(3) * uy * Lw;
+  const R Bz = fmadd(w1, B1z, w2 * B2z) - R(3) * uz * Lw;
+  const R dtau_local = omega * omega * dt;
+  if (store) {
+    // mu_j = (1-omega) lam_j + omega (S0 + (c_j - u).B) + pg (c_j - u).axis
+    //      = (1-omega) lam_j + T0 + c_j.E
+    R uax, ax[3];
+    probe_axis<R>(pm, ax);
+    Macro<R> m;
+    m.drho = drho;
+    m.rho = rho;
+    m.ux = ux;
+    m.uy = uy;
+    m.uz = uz;
+    const R pg = probe_term<R>(pm, x, m, &uax, true);
+    const R Ex = omega * Bx + pg * ax[0], Ey = omega * By + pg * ax[1], Ez = omega * Bz + pg * ax[2];
+    const R T0 = omega * (S0 - ux * Bx - uy * By - uz * Bz) - pg * uax;
+    const R om1 = R(1) - omega;
+    *(mu_out + xi) = from_real<S>(fmadd(om1, lam[0], T0));
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const R cu = cdotu<R>(i, m.ux, m.uy, m.uz);
-      const R w = wgt<R>(i);
-      S0 += lam[i] * w * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq15);  // feq_i / rho
-      Lw += lam[i] * w;
-      const R b = lam[i] * w * (R(3) + R(9) * cu);
-      if (cx(i)) Bx += cx(i) > 0 ? b : -b;
-      if (cy(i)) By += cy(i) > 0 ? b : -b;
-      if (cz(i)) Bz += cz(i) > 0 ? b : -b;
-      dt += lam[i] * neq[i][threadIdx.x];
-    }
-    Bx -= R(3) * m.ux * Lw;
-    By -= R(3) * m.uy * Lw;
-    Bz -= R(3) * m.uz * Lw;
-    dtau_local = (double)(omega * omega * dt);
-    if (store) {
-      // mu_j = (1-omega) lam_j + omega (S0 + (c_j - u).B) + pg (c_j - u).axis
-      //      = (1-omega) lam_j + T0 + c_j.E
-      R uax;
-      const R pg = probe_term<R>(pm, x, m, &uax, true);
-      const R Ex = omega * Bx + pg * R(pm.ax), Ey = omega * By + pg * R(pm.ay), Ez = omega * Bz + pg * R(pm.az);
-      const R T0 = omega * (S0 - m.ux * Bx - m.uy * By - m.uz * Bz) - pg * uax;
-#pragma unroll
-      for (int j = 0; j < Q; ++j) {
-        R v = (R(1) - omega) * lam[j] + T0;
-        if (cx(j)) v += cx(j) > 0 ? Ex : -Ex;
-        if (cy(j)) v += cy(j) > 0 ? Ey : -Ey;
-        if (cz(j)) v += cz(j) > 0 ? Ez : -Ez;
-        *(j == 0 ? mu_out + xi : at<WIDE>(mu_out, j, n, slot<WIDE>(j, n, xi))) = from_real<S>(v);
-      }
+    for (int p = 0; p < 9; ++p) {
+      const int i = 2 * p + 1;
+      const R ce = cdotu<R>(i, Ex, Ey, Ez);
+      *at<WIDE>(mu_out, i, n, slot<WIDE>(i, n, xi)) = from_real<S>(fmadd(om1, lam[i], T0 + ce));
+      *at<WIDE>(mu_out, i, n, slot<WIDE>(i + 1, n, xi)) = from_real<S>(fmadd(om1, lam[i + 1], T0 - ce));
     }
   }
   return dtau_local;
@@ -200,7 +314,7 @@ __device__ __forceinline__ void warp_moment_sums(R v, int i, R* d, R* jx, R* jy,
 // s'(t) at the site), applies the collision transpose, and accumulates the
 // per-link amplitude derivatives (each link record belongs to one lane).
 template <typename S, bool GPREV>
-__device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev, const S* __restrict__ cur,
+__device__ __forceinline__ typename Real<S>::type adjoint_iolet_site(const S* __restrict__ prev, const S* __restrict__ cur,
                                                      const S* __restrict__ mu_next, S* __restrict__ mu_out,
                                                      const int32_t* __restrict__ src,
                                                      const LinkRec* __restrict__ links,
@@ -212,7 +326,7 @@ __device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev,
   const StepParams& p = ap.prev;
   const int i = threadIdx.x & 31;
   const bool dir = i < Q;
-  double dtau_local = 0;
+  R dtau_local = R(0);
   if (w < nsites) {  // uniform across the warp
     const int64_t n = p.n, x = sites[w];
     const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
@@ -312,13 +426,15 @@ __device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev,
     Bx -= R(3) * m.ux * Lw;
     By -= R(3) * m.uy * Lw;
     Bz -= R(3) * m.uz * Lw;
-    if (i == 0) dtau_local = (double)(omega * omega * dt);
+    if (i == 0) dtau_local = omega * omega * dt;
     if (store && dir) {
       R uax;
       const R pg = probe_term<R>(pm, x, m, &uax, i == 0);
       R v = (R(1) - omega) * lam +
             omega * (S0 + (R(k_cx[i]) - m.ux) * Bx + (R(k_cy[i]) - m.uy) * By + (R(k_cz[i]) - m.uz) * Bz);
-      v += pg * (R(k_cx[i]) * R(pm.ax) + R(k_cy[i]) * R(pm.ay) + R(k_cz[i]) * R(pm.az) - uax);
+      R ax[3];
+      probe_axis<R>(pm, ax);
+      v += pg * (R(k_cx[i]) * ax[0] + R(k_cy[i]) * ax[1] + R(k_cz[i]) * ax[2] - uax);
       mu_out[(int64_t)i * n + x] = from_real<S>(v);
     }
   }
@@ -333,27 +449,32 @@ __device__ __forceinline__ double adjoint_iolet_site(const S* __restrict__ prev,
 // WIDE: offsets within direction pairs (lattices above ~226M sites); the
 // offsets stay 32-bit either way, which keeps the 38 gather addresses from
 // spilling.
-template <typename S, bool GPREV, bool WIDE>
+template <typename S, bool GPREV, bool WIDE, bool CT>
 __global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2 : 4)
     k_adjoint(const S* __restrict__ prev, const S* __restrict__ cur, const S* __restrict__ mu_next,
-              S* __restrict__ mu_out, const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
-              const double* __restrict__ amp, const AdjParams ap, const ProbeMap pm,
-              const int32_t* __restrict__ sites, int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
-              double* __restrict__ part, double* __restrict__ dlink, int store) {
+              S* __restrict__ mu_out, const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
+              const int32_t* __restrict__ tbase, const uint32_t* __restrict__ imask,
+              const LinkRec* __restrict__ links, const double* __restrict__ amp, const AdjParams ap,
+              const ProbeMap pm, const int32_t* __restrict__ sites, int64_t nsites, unsigned n_iolet_blocks,
+              unsigned stride, double* __restrict__ part, double* __restrict__ dlink, int store) {
   using R = typename Real<S>::type;
   __shared__ R neq[Q][BLOCK];
-  __shared__ double sh[BLOCK / 32];
+  __shared__ R sh[BLOCK / 32];
   const unsigned b = blockIdx.x, j = b / stride;
-  double d;
+  R d;
   if (b % stride == 0 && j < n_iolet_blocks) {
     d = adjoint_iolet_site<S, GPREV>(prev, cur, mu_next, mu_out, src, links, amp, ap, pm, sites, nsites, dlink,
                                      store, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
   } else {
     const unsigned k = b - min(n_iolet_blocks, j + 1);  // bulk block: blocks before b that are not iolet blocks
-    d = adjoint_site<S, GPREV, WIDE>(prev, mu_next, mu_out, src, ap, pm, store, (int64_t)k * BLOCK + threadIdx.x, neq);
+    d = adjoint_site<S, GPREV, WIDE, CT>(prev, mu_next, mu_out, src, ctab, tbase, imask, ap, pm, store,
+                                         (int64_t)k * BLOCK + threadIdx.x, k, neq);
   }
-  const double bs = block_sum(d, sh);
-  if (threadIdx.x == 0) part[b] += bs;
+  // block sum of the dJ/dtau terms in the kernel's arithmetic type (FP64 on
+  // GB300 runs at 1/64 of the FP32 rate), accumulated per block in FP64
+  // across the reverse steps
+  const R bs = block_sum_r<R>(d, sh);
+  if (threadIdx.x == 0) part[b] += (double)bs;
 }
 
 // The objective's last term, t = N: J gains (u.axis - target)^2 / N and
@@ -416,12 +537,16 @@ cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, co
   const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // one warp per iolet site
   const unsigned grid = gi + grid_for(h->n);
   const unsigned stride = gi ? grid / gi : 1;  // gi * stride <= grid
-  const bool off32 = h->off32;
-  auto kernel = gprev ? (off32 ? k_adjoint<S, true, false> : k_adjoint<S, true, true>)
-                      : (off32 ? k_adjoint<S, false, false> : k_adjoint<S, false, true>);
-  kernel<<<grid, BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src, h->d_links,
-                                 h->d_amp, ap, pm, h->d_iolet_sites, h->n_iolet_sites, gi, stride, dtau_part, dlink,
-                                 st_);
+  const bool off32 = h->off32, ct = h->compact;
+  auto pick = [&](auto gp) {
+    constexpr bool G = decltype(gp)::value;
+    return ct ? (off32 ? k_adjoint<S, G, false, true> : k_adjoint<S, G, true, true>)
+              : (off32 ? k_adjoint<S, G, false, false> : k_adjoint<S, G, true, false>);
+  };
+  auto kernel = gprev ? pick(std::true_type{}) : pick(std::false_type{});
+  kernel<<<grid, BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src, h->d_ctab,
+                                 h->d_tbase, h->d_imask, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
+                                 h->n_iolet_sites, gi, stride, dtau_part, dlink, st_);
   return cudaGetLastError();
 }
 
@@ -542,7 +667,8 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   }
   TRY(cudaMemcpyAsync(d_mask, mask.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, st));
   TRY(cudaMemcpyAsync(d_base, base.data(), sizeof(int32_t) * nw, cudaMemcpyHostToDevice, st));
-  const ProbeMap pm{d_mask, d_base, d_target, jp, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N};
+  const ProbeMap pm{d_mask, d_base, d_target, jp, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N,
+                    (float)obj->axis[0], (float)obj->axis[1], (float)obj->axis[2]};
   TRY(cudaMemcpyAsync(gbegin, h->group_link_begin.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, st));
   Probe pr{d_sites, d_target, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N, np};
 

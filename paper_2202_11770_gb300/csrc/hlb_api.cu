@@ -213,12 +213,13 @@ int validate(const hlb_lattice* L, const hlb_options* o, std::vector<int64_t>* p
 }
 
 // AUTO resolves to the scheme measured faster on GB300 for the lattice size.
-// The AA pattern moves 188 B per FP32 site update against 224 B for pull
-// A-B, but needs a second launch per step for its iolet-site pass (about
-// 20 us of latency-bound work whatever the size).  Per step, AA took 28 ps
-// per site + ~21 us and A-B 34 ps per site + ~2 us, so AA wins above about
-// 3.2M sites: 2.0M sites 79 vs 77 us, 20M sites 585 vs 682 us.
-constexpr int64_t AA_MIN_SITES = 4000000;
+// The AA pattern moves 170 B per FP32 site update against 188 B for pull
+// A-B (compact index table), but needs a second launch per step for its
+// iolet-site pass.  Measured per step (seeded vessel trees, FP32 / BF16):
+// 0.5M sites A-B 13.4 / 12.0 us, AA 14.8 / 12.6 us (the state fits in L2);
+// 1.0M sites A-B 32.4 / 23.8 us, AA 29.8 / 19.9 us; 2.0M 67.7 / 49.4 against
+// 61.7 / 42.3 us; 8.0M 256 / 188 against 229 / 145 us.  AA from 750k sites.
+constexpr int64_t AA_MIN_SITES = 750000;
 int32_t resolve_scheme(int32_t scheme, int64_t n) {
   if (scheme != HLB_SCHEME_AUTO) return scheme;
   return n >= AA_MIN_SITES ? HLB_AA : HLB_PULL_AB;

@@ -24,6 +24,8 @@ static __device__ __align__(256) double g_partials[MAX_PARTIALS];
 
 // Device address of g_partials per device ordinal, looked up once with that
 // device current (in host code the symbol itself is only a host stand-in).
+// It belongs to the device's primary context: after a cudaDeviceReset it is
+// stale, which the header states as a condition of use.
 constexpr int MAX_DEVICES = 64;
 void* g_addr[MAX_DEVICES] = {};
 std::mutex g_mutex;

@@ -25,15 +25,30 @@ def _mass_static(state, precision, n, out, stream):
                                             C.c_void_p(out.data_ptr()), C.c_void_p(stream))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-12), ("bf16", 1e-12), ("fp64", 1e-13)])
-def test_static_mass_matches_reduce_twice(prec, tol):
+def _iolet_rounding_bound(state, lat, prec):
+    """Sum over the iolet links of half a unit in the last place of their
+    stored values: for a 16-bit state read back after a pull A-B step, the
+    read-back rounds the boundary values of these links to the storage format,
+    which the workspace-based reduction sums unrounded."""
+    if prec not in ("bf16", "fp16") or state is None:
+        return 0.0
+    vals = state.float().cpu().numpy()[1:][lat.src <= -2].astype(np.float64)
+    mant = 7 if prec == "bf16" else 10
+    e = np.floor(np.log2(np.maximum(np.abs(vals), 2.0 ** -24)))
+    return float((0.5 * 2.0 ** (e - mant)).sum())
+
+
+@pytest.mark.parametrize("prec,scheme,tol", [("fp32", "aa", 1e-12), ("bf16", "aa", 1e-12), ("fp64", "aa", 1e-13),
+                                             ("fp32", "ab", 1e-12), ("bf16", "ab", 1e-12), ("fp16", "ab", 1e-12),
+                                             ("fp16", "aa", 1e-12)])
+def test_static_mass_matches_reduce_twice(prec, scheme, tol):
     lat = geo.tree(2, 2202, target_sites=50_000, length_ratio=5.0)
-    s = hemegb.Solver(lat, tau=0.6, precision=prec, scheme="aa")
+    s = hemegb.Solver(lat, tau=0.6, precision=prec, scheme=scheme)
     s.set_velocity(0, [1.0], {"kind": "cosine", "mean": 0.02, "rel": 0.5, "period": 100.0})
     for k in range(1, len(lat.iolets)):
         s.set_pressure(k, 1.0 - 0.0005 * k)
     s.init_equilibrium()
-    elem = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp64": torch.float64}[prec]
+    elem = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16, "fp64": torch.float64}[prec]
     state = torch.empty((19, lat.n), dtype=elem, device="cuda")
     out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
     stream = s.stream.cuda_stream
@@ -45,7 +60,8 @@ def test_static_mass_matches_reduce_twice(prec, tol):
         assert _mass_static(state, s.precision, lat.n, out[call:], stream) == hemegb.HLB_OK
         torch.cuda.synchronize()
         got = float(out[call].item())
-        assert abs(got - mass_ref) <= tol * mass_ref, (call, got, mass_ref)
+        bound = tol * mass_ref + (_iolet_rounding_bound(state, lat, prec) if scheme == "ab" else 0.0)
+        assert abs(got - mass_ref) <= bound, (call, got, mass_ref, bound)
     assert float(out[0]) != float(out[1])      # two different states, two fresh results
 
 
