@@ -303,6 +303,8 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   const int64_t n = L->n_sites;
   h->n = n;
   h->sn = row_stride(n);
+  h->owned_lo = 0;
+  h->owned_hi = n;
   h->n_iolets = L->n_iolets;
   h->iolets.assign(L->iolets, L->iolets + L->n_iolets);
   h->precision = o->precision;

@@ -596,17 +596,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
-// Per-block sums of drho (mass - n) into part[blockIdx.x].
+// Per-block sums of drho (mass - sites) over the sites [lo, hi) into
+// part[blockIdx.x].
 template <typename S, int MODE>
 __global__ void __launch_bounds__(BLOCK) k_mass(const S* __restrict__ fin, const int32_t* __restrict__ src,
                                                 const LinkRec* __restrict__ links,
-                                                const double* __restrict__ amp, const StepParams p,
-                                                double* __restrict__ part) {
+                                                const double* __restrict__ amp, const StepParams p, int64_t lo,
+                                                int64_t hi, double* __restrict__ part) {
   using R = typename Real<S>::type;
   __shared__ double sh[BLOCK / 32];
-  const int64_t x = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int64_t x = lo + (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   double d = 0;
-  if (x < p.n) {
+  if (x < hi) {
     R h[Q];
     load_state<S, MODE>(fin, src, links, amp, p, x, h);
 #pragma unroll
@@ -941,10 +942,11 @@ struct ReduceOp {
                          cudaStream_t s) {
     StepParams p = h->params(tb);
     const int64_t nb = grid_for(h->n);
+    const int64_t lo = h->owned_lo, hi = h->owned_hi, nbo = grid_for(hi - lo);
     double* part = h->d_red;
-    HLB_MODE_SWITCH(mode, (k_mass<S, M><<<(unsigned)nb, BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links,
-                                                                         h->d_amp, p, part)));
-    k_finish<<<1, 1024, 0, s>>>(part, nb, h->n, out);
+    HLB_MODE_SWITCH(mode, (k_mass<S, M><<<(unsigned)nbo, BLOCK, 0, s>>>((const S*)fin, h->d_src, h->d_links,
+                                                                          h->d_amp, p, lo, hi, part)));
+    k_finish<<<1, 1024, 0, s>>>(part, nbo, hi - lo, out);
     if (h->n_iolets > 0) {
       const int64_t* begin = (const int64_t*)(h->d_red + nb);  // link ranges stored after the partials
       if (!have_flux)

@@ -27,6 +27,7 @@ struct hlb_solver {
   // lattice
   int64_t n = 0;
   int64_t sn = 0;                     // index-table row stride: n rounded up to a multiple of 4
+  int64_t owned_lo = 0, owned_hi = 0; // sites counted by the mass reduction (a part's own sites)
   int32_t n_iolets = 0;
   std::vector<hlb_iolet> iolets;
   std::vector<int32_t> group_offset;  // per iolet: first global amplitude group (-1: pressure)

@@ -28,6 +28,16 @@ def test_solver_library_exports_declared_symbols():
     assert sorted(names) == hemegb.exported_symbols()
 
 
+def test_partition_symbols_exported():
+    from paper_2202_11770_gb300 import partition
+    lib = partition.library()
+    names = _declared("hlb_partition.h")
+    assert "hlb_part_create" in names and "hlb_halo_pack" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(names) == partition.exported_symbols()
+
+
 def test_geometry_library_exports_declared_symbols():
     lib = C.CDLL(str(_build.build_geometry()))
     for name in _declared("hlb_geometry.h"):
