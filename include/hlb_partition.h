@@ -73,6 +73,21 @@ int hlb_part_ghosts(const hlb_part* plan, int32_t q, int32_t p, int64_t* n, cons
 int hlb_halo_pack(hlb_solver* h, const int64_t* slots, int64_t n, void* buf);
 int hlb_halo_unpack(hlb_solver* h, const int64_t* slots, int64_t n, const void* buf);
 
+/* Part of one pull A-B step (after the solver's first step), for the edge-
+ * first order of a partitioned run (Section 3.2.3): the step of the sites in
+ * the 256-site tiles [first_tile, first_tile + n_tiles) and, with
+ * iolet_sites != 0, of the sites with iolet links.  The ranges of one step
+ * must cover every tile once and the iolet sites once; the call with
+ * finish != 0, the last of the step, advances the solver to the next time.
+ * Launches in stream order on the solver's stream; between the calls the
+ * caller may pack the halo of the tiles already stepped (hlb_set_stream
+ * moves the solver to another stream); hlb_halo_pack and hlb_halo_unpack
+ * then address the state being written.  Until the finishing call, no other
+ * call reads or steps the solver (hlb_step returns HLB_ERR_STATE).
+ * HLB_ERR_STATE for an AA solver, before the first step, or with Windkessel
+ * outlets. */
+int hlb_step_range(hlb_solver* h, int64_t first_tile, int64_t n_tiles, int32_t iolet_sites, int32_t finish);
+
 /* Restrict the total mass of hlb_reduce to the local sites [lo, hi): a
  * part's owned sites.  The iolet fluxes need no restriction (ghosts carry no
  * iolet links).  A new solver counts all its sites. */

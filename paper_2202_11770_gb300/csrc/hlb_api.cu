@@ -650,6 +650,7 @@ extern "C" int hlb_init_equilibrium(hlb_solver* h, double rho0, const float* u0,
 extern "C" int hlb_step(hlb_solver* h, int64_t nsteps) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
   if (nsteps < 0) return hlb_fail(HLB_ERR_ARG, "negative step count");
+  if (h->midstep) return hlb_fail(HLB_ERR_STATE, "a partial step (hlb_step_range) is not finished");
   for (int64_t s = 0; s < nsteps; ++s) {
     if (h->scheme == HLB_AA) {
       // even step from f(t) in place, odd step from the swapped buffer

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
                                                 const int32_t* __restrict__ tbase, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
                                                 int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
-                                                const uint32_t* __restrict__ imask, uint32_t pf, const StepParams p) {
+                                                const uint32_t* __restrict__ imask, uint32_t pf, uint32_t tile0,
+                                                const StepParams p) {
   using R = typename Real<S>::type;
   const unsigned b = blockIdx.x, j = b / stride;
   if (b % stride == 0 && j < n_iolet_blocks) {
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
     return;
   }
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
-  const uint32_t tile = b - min(n_iolet_blocks, j + 1);
+  const uint32_t tile = tile0 + b - min(n_iolet_blocks, j + 1);
   const uint32_t x = tile * BLOCK + threadIdx.x;
   if (CT && pf && threadIdx.x < 32) prefetch_tile<S, sizeof(S) >= 4, false>(fin, ctab, tbase, n, sn, tile + pf);
   uint32_t off[Q];
@@ -698,21 +699,37 @@ cudaError_t dispatch(int precision, A... a) {
   return cudaErrorInvalidValue;
 }
 
+// One pull A-B gather step over the bulk tiles [tile0, tile0 + ntiles) and,
+// with `iolets`, the iolet sites (the whole step: tile0 = 0, all tiles).
+template <typename S>
+cudaError_t launch_gather(const hlb_solver* h, const void* fin, void* fout, const StepParams& p, uint32_t tile0,
+                          uint32_t ntiles, bool iolets, cudaStream_t s) {
+  const unsigned gi = iolets ? (unsigned)((h->n_iolet_sites + 7) / 8) : 0u;  // 8 warps (sites) per block
+  const unsigned grid = gi + ntiles;
+  if (grid == 0) return cudaSuccess;
+  auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
+                           : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
+  return launch_pdl(kernel, grid, BLOCK, s, (const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase, h->d_links,
+                    h->d_amp, h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, h->d_imask,
+                    (uint32_t)h->n_sm * 5u, tile0, p);
+}
+
 template <typename S>
 struct StepOp {
   static cudaError_t run(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
                          cudaStream_t s) {
     StepParams p = h->params(tb);
-    if (gather) {
-      const unsigned gi = (unsigned)((h->n_iolet_sites + 7) / 8);  // 8 warps (sites) per block
-      const unsigned grid = gi + grid_for(h->n);
-      auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
-                               : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
-      return launch_pdl(kernel, grid, BLOCK, s, (const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase,
-                        h->d_links, h->d_amp, h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, h->d_imask,
-                        (uint32_t)h->n_sm * 5u, p);
-    }
+    if (gather) return launch_gather<S>(h, fin, fout, p, 0, grid_for(h->n), true, s);
     return launch_pdl(k_step_local<S>, grid_for(h->n), BLOCK, s, (const S*)fin, (S*)fout, p);
+  }
+};
+
+template <typename S>
+struct StepRangeOp {
+  static cudaError_t run(const hlb_solver* h, const void* fin, void* fout, int64_t tb, int64_t tile0,
+                         int64_t ntiles, bool iolets, cudaStream_t s) {
+    StepParams p = h->params(tb);
+    return launch_gather<S>(h, fin, fout, p, (uint32_t)tile0, (uint32_t)ntiles, iolets, s);
   }
 };
 
@@ -972,6 +989,10 @@ int64_t hlb_reduce_slots(int64_t n, int32_t n_iolets) {
 cudaError_t hlb_launch_step(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
                             cudaStream_t s) {
   return dispatch<StepOp>(h->precision, h, fin, fout, gather, tb, s);
+}
+cudaError_t hlb_launch_step_range(const hlb_solver* h, const void* fin, void* fout, int64_t tb, int64_t tile0,
+                                  int64_t ntiles, bool iolets, cudaStream_t s) {
+  return dispatch<StepRangeOp>(h->precision, h, fin, fout, tb, tile0, ntiles, iolets, s);
 }
 cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s) {
   return dispatch<AAOp>(h->precision, h, A, odd, t, s);

@@ -53,6 +53,7 @@ struct hlb_solver {
   int phase = 0;                      // HLB_READ_LOCAL: f(t) in place; GATHER_AB: s'(t-1); GATHER_AA: AA after an even step
   int64_t t = 0;
   bool stepped = false;               // f(t) came from a step (iolet fluxes defined)
+  bool midstep = false;               // between the calls of one hlb_step_range step: f[cur ^ 1] is being written
   double tau = 1.0;
   std::vector<HostWave> wave;         // per iolet
   std::vector<double> amp;            // per global group
@@ -118,6 +119,10 @@ int hlb_no_throw(F f) {
 // One pull A-B time step from fin into fout (gather: fin holds s'(t-1)).
 cudaError_t hlb_launch_step(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
                             cudaStream_t s);
+// Part of a pull A-B gather step: bulk tiles [tile0, tile0 + ntiles) of 256
+// sites and, with `iolets`, the iolet sites.
+cudaError_t hlb_launch_step_range(const hlb_solver* h, const void* fin, void* fout, int64_t tb, int64_t tile0,
+                                  int64_t ntiles, bool iolets, cudaStream_t s);
 // One AA time step at time t on buffer A (odd: the buffer is in the swapped phase).
 cudaError_t hlb_launch_aa(const hlb_solver* h, void* A, bool odd, int64_t t, cudaStream_t s);
 // rho, u [3][n], wss of the current state, device outputs (any may be null).

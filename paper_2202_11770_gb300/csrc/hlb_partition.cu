@@ -174,11 +174,13 @@ cudaError_t halo_copy(bool pack, void* f, const int64_t* slots, int64_t n, void*
 
 int halo_impl(hlb_solver* h, const int64_t* slots, int64_t n, void* buf, bool pack) {
   if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  // pack / unpack address the post-collision state of the step in progress
+  // (mid-step) or of the last step
   if (n < 0 || (n > 0 && (!slots || !buf))) return hlb_fail(HLB_ERR_ARG, "bad halo arrays");
   if (h->scheme != HLB_PULL_AB || h->phase != HLB_READ_GATHER_AB)
     return hlb_fail(HLB_ERR_STATE, "halo exchange needs a pull A-B solver after a step");
   if (n == 0) return HLB_OK;
-  void* f = h->f[h->cur];
+  void* f = h->f[h->midstep ? h->cur ^ 1 : h->cur];  // mid-step: the state being written
   cudaError_t e;
   switch (h->elem_bytes()) {
     case 2: e = halo_copy<uint16_t>(pack, f, slots, n, buf, h->stream); break;
@@ -256,5 +258,25 @@ extern "C" int hlb_set_owned_range(hlb_solver* h, int64_t lo, int64_t hi) {
   if (lo < 0 || hi > h->n || lo >= hi) return hlb_fail(HLB_ERR_ARG, "owned range must satisfy 0 <= lo < hi <= n");
   h->owned_lo = lo;
   h->owned_hi = hi;
+  return HLB_OK;
+}
+
+extern "C" int hlb_step_range(hlb_solver* h, int64_t first_tile, int64_t n_tiles, int32_t iolet_sites,
+                              int32_t finish) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (h->scheme != HLB_PULL_AB || h->phase != HLB_READ_GATHER_AB)
+    return hlb_fail(HLB_ERR_STATE, "a partial step needs a pull A-B solver after a step");
+  if (h->any_wk()) return hlb_fail(HLB_ERR_STATE, "a partial step does not update Windkessel outlets");
+  const int64_t tiles = (h->n + 255) / 256;
+  if (first_tile < 0 || n_tiles < 0 || first_tile + n_tiles > tiles) return hlb_fail(HLB_ERR_ARG, "tile range out of bounds");
+  const cudaError_t e = hlb_launch_step_range(h, h->f[h->cur], h->f[h->cur ^ 1], h->t - 1, first_tile, n_tiles,
+                                              iolet_sites != 0, h->stream);
+  if (e != cudaSuccess) return hlb_cuda_fail(e, "hlb_step_range");
+  h->midstep = !finish;
+  if (finish) {
+    h->cur ^= 1;
+    h->t += 1;
+    h->stepped = true;
+  }
   return HLB_OK;
 }

@@ -45,6 +45,7 @@ _PROTOS = {
     "hlb_halo_pack": (C.c_int, [_P, _P, C.c_int64, _P]),
     "hlb_halo_unpack": (C.c_int, [_P, _P, C.c_int64, _P]),
     "hlb_set_owned_range": (C.c_int, [_P, C.c_int64, C.c_int64]),
+    "hlb_step_range": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int32, C.c_int32]),
 }
 _bound = False
 
@@ -201,13 +202,30 @@ class HaloExchange:
             unpack(q, self.recv_idx[q], recv[q])
 
 
+def _runs(tiles):
+    """Sorted tile numbers -> [(first, count)] of consecutive runs."""
+    out = []
+    for t in tiles:
+        if out and out[-1][0] + out[-1][1] == t:
+            out[-1][1] += 1
+        else:
+            out.append([int(t), 1])
+    return [tuple(r) for r in out]
+
+
 class PartitionedSolver:
     """All parts of an ``n_parts`` slab decomposition on the current GPU, one
     process: every step runs a pull A-B step of each part, then copies the
     post-collision halo values from their owners into the ghosts, device to
     device (hlb_halo_pack / hlb_halo_unpack).  The owned states, and so the
     macroscopic fields, mass and iolet fluxes, equal the undivided solver's
-    bit for bit."""
+    bit for bit.
+
+    With ``overlap`` (the paper's edge-first order, Section 3.2.3), a step
+    first runs each part's edge tiles (the 256-site tiles holding the sites
+    whose values other parts pull, or ghosts, and the iolet sites), then packs
+    and unpacks the halo on a second stream while the interior tiles run on
+    the solver stream; the next step waits for both."""
 
     def __init__(self, lattice, n_parts: int, tau=1.0, precision="fp32", **kw):
         import torch
@@ -230,6 +248,7 @@ class PartitionedSolver:
         elem = {hemegb.HLB_FP32: torch.float32, hemegb.HLB_FP64: torch.float64, hemegb.HLB_BF16: torch.bfloat16,
                 hemegb.HLB_FP16: torch.float16}[self.precision]
         self._links = []  # (q, p, src slots, dst slots, buffer) on the device
+        send_sites = [set() for _ in range(self.n_parts)]
         for p in range(self.n_parts):
             for q in range(self.n_parts):
                 if q == p:
@@ -238,6 +257,21 @@ class PartitionedSolver:
                 if a.size:
                     self._links.append((q, p, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(),
                                         torch.empty(a.size, dtype=elem, device="cuda")))
+                    send_sites[q].update((a % self.parts[q].n).tolist())
+        # tile runs of each part: edge (holding sites others pull, or ghosts,
+        # whose slots the exchange writes and the step must not overwrite
+        # after it) and interior
+        self._edge, self._interior = [], []
+        for p, s in enumerate(self.parts):
+            tiles = (s.n + 255) // 256
+            lo, hi = self.owned[p]
+            ghost_tiles = set(range(0, (lo + 255) // 256)) | set(range(hi // 256, tiles))
+            edge = sorted({x // 256 for x in send_sites[p]} | ghost_tiles)
+            eset = set(edge)
+            self._edge.append(_runs(edge))
+            self._interior.append(_runs([t for t in range(tiles) if t not in eset]))
+        self._side = torch.cuda.Stream()
+        self._fresh = True   # the next step is the first after init / set_state (a plain step)
 
     # ---- parameters, forwarded to every part ----
     def set_tau(self, tau):
@@ -255,6 +289,7 @@ class PartitionedSolver:
     def init_equilibrium(self, rho0=1.0, u0=None):
         for p, s in enumerate(self.parts):
             s.init_equilibrium(rho0, None if u0 is None else np.ascontiguousarray(np.asarray(u0)[:, self.glob[p]]))
+        self._fresh = True
 
     # ---- stepping ----
     def exchange(self):
@@ -262,11 +297,41 @@ class PartitionedSolver:
             _check(self._lib.hlb_halo_pack(self.parts[q].handle, _P(a.data_ptr()), a.numel(), _P(buf.data_ptr())))
             _check(self._lib.hlb_halo_unpack(self.parts[p].handle, _P(b.data_ptr()), b.numel(), _P(buf.data_ptr())))
 
-    def step(self, n=1):
+    def step(self, n=1, overlap=False):
         for _ in range(int(n)):
-            for s in self.parts:
-                s.step(1)
-            self.exchange()
+            if overlap and not self._fresh:
+                self._step_overlapped()
+            else:
+                for s in self.parts:
+                    s.step(1)
+                self.exchange()
+            self._fresh = False
+
+    def _step_overlapped(self):
+        torch, lib = self._torch, self._lib
+        main = self.parts[0].stream
+        for p, s in enumerate(self.parts):
+            for k, (a, cnt) in enumerate(self._edge[p]):
+                last = k == len(self._edge[p]) - 1 and not self._interior[p]
+                _check(lib.hlb_step_range(s.handle, a, cnt, int(k == 0), int(last)))
+            if not self._edge[p] and not self._interior[p]:
+                raise RuntimeError("empty part")
+        edges_done = torch.cuda.Event()
+        edges_done.record(main)
+        self._side.wait_event(edges_done)
+        for s in self.parts:
+            _check(lib.hlb_set_stream(s.handle, _P(self._side.cuda_stream)))
+        self.exchange()
+        for s in self.parts:
+            _check(lib.hlb_set_stream(s.handle, _P(main.cuda_stream)))
+        halo_done = torch.cuda.Event()
+        halo_done.record(self._side)
+        for p, s in enumerate(self.parts):
+            runs = self._interior[p]
+            for k, (a, cnt) in enumerate(runs):
+                _check(lib.hlb_step_range(s.handle, a, cnt, int(not self._edge[p] and k == 0),
+                                          int(k == len(runs) - 1)))
+        main.wait_event(halo_done)
 
     @property
     def t(self):

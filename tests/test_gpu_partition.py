@@ -53,6 +53,26 @@ def test_partitioned_run_is_bit_identical(tree, n_parts, prec):
     assert np.allclose(fl, fl_ref, rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("n_parts", [2, 5])
+def test_edge_first_overlapped_steps_are_bit_identical(tree, n_parts):
+    """The edge-first order: edge tiles, then the halo exchange on a second
+    stream while the interior tiles run (hlb_step_range)."""
+    lat = tree
+    ref = hemegb.Solver(lat, tau=0.6, precision="fp32", scheme="ab")
+    ps = partition.PartitionedSolver(lat, n_parts, tau=0.6, precision="fp32")
+    _bc(ref, lat)
+    _bc(ps, lat)
+    ref.init_equilibrium()
+    ps.init_equilibrium()
+    ref.step(37)
+    ps.step(37, overlap=True)
+    assert all(len(e) and len(i) for e, i in zip(ps._edge, ps._interior))
+    assert ps.state()[0].tobytes() == ref.state()[0].tobytes()
+    m, fl = ps.reduce()
+    m_ref, fl_ref = ref.reduce()
+    assert abs(m - m_ref) <= 1e-12 * m_ref and np.allclose(fl, fl_ref, rtol=1e-12, atol=1e-15)
+
+
 def test_partitioned_pipe_inlet_and_outlet_in_different_parts():
     lat = geo.pipe(8.0, 64)
     ref = hemegb.Solver(lat, tau=0.8, precision="fp32", scheme="ab")
