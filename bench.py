@@ -27,6 +27,7 @@ oracle on a 1M-site tree after 1,000 steps (``precision_vs_oracle``).
 from __future__ import annotations
 
 import argparse
+import ctypes as C
 import hashlib
 import json
 import math
@@ -418,6 +419,64 @@ def cpu_baseline(lat, steps_1, steps_all, pipe_steps):
                            "seconds": [round(pd1, 2), round(pdn, 2)]}}
 
 
+def split_kernels(lat, steps, torch):
+    """The paper's per-site-type kernels on streams (Section 3.2.2) against
+    the fused kernel, FP32 pull A-B: the fused kernel on the (z, y, x) site
+    order; the fused kernel on the sites sorted by type (the order the
+    per-type kernels need); one launch per type range, each on its own
+    stream (hlb_step_range over the 256-site tiles of the range)."""
+    from paper_2202_11770_gb300 import hemegb, partition, workloads
+    lib = partition.library()
+    sorted_lat, ranges = workloads.type_sorted(lat)
+    out = {"types": {str(t): e - b for t, b, e in ranges}}
+
+    def run(lattice, label, per_type=None, full_index=False):
+        s = hemegb.Solver(lattice, tau=0.55, precision="fp32", scheme="ab", full_index=full_index)
+        set_bc(s, lattice)
+        s.init_equilibrium()
+        s.step(5)
+        main = s.stream
+        streams = [torch.cuda.Stream() for _ in (per_type or [])]
+        tiles = (lattice.n + 255) // 256
+        cuts = sorted({0, tiles} | {min(tiles, b // 256) for _, b, _ in (per_type or [])})
+        chunks = [(a, b - a) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for _ in range(steps):
+            if per_type is None:
+                s.step(1)
+                continue
+            start = torch.cuda.Event()
+            start.record(main)
+            done = []
+            for k, (a, cnt) in enumerate(chunks):
+                st = streams[k % len(streams)]
+                st.wait_event(start)
+                lib.hlb_set_stream(s.handle, C.c_void_p(st.cuda_stream))
+                rc = lib.hlb_step_range(s.handle, a, cnt, int(k == 0), int(k == len(chunks) - 1))
+                assert rc == 0, lib.hlb_last_error()
+                ev = torch.cuda.Event()
+                ev.record(st)
+                done.append(ev)
+            for ev in done:
+                main.wait_event(ev)
+            lib.hlb_set_stream(s.handle, C.c_void_p(main.cuda_stream))
+        e1.record(main)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / steps * 1e3
+        out[label] = {"us_per_step": us, "index": "compact" if s.compact_index else "int32",
+                      "launches_per_step": 1 if per_type is None else len(chunks)}
+        del s
+        torch.cuda.empty_cache()
+
+    run(lat, "fused_zyx")
+    run(lat, "fused_zyx_int32", full_index=True)
+    run(sorted_lat, "fused_type_sorted")
+    run(sorted_lat, "per_type_streams", per_type=ranges)
+    return out
+
+
 def precision_vs_oracle(sites, steps, torch, forms=(("fp32", "ab"), ("fp32", "aa"), ("bf16", "ab"), ("bf16", "aa"),
                                                      ("fp16", "ab"), ("fp16", "aa"))):
     """Velocity and wall-shear-stress error of each storage form against the
@@ -604,6 +663,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-sites", type=int, default=2_000_000)
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint/forward timing")
+    ap.add_argument("--split-kernels", action="store_true",
+                    help="the paper's per-site-type kernels on streams against the fused kernel (FP32 pull A-B)")
     ap.add_argument("--precision-study", action="store_true",
                     help="u and WSS error of FP32/BF16/FP16 storage vs FP64 at 1k, 5k, 10k steps")
     ap.add_argument("--ref-steps", type=int, default=3)
@@ -631,6 +692,12 @@ def main():
         print(json.dumps({"precision_study": res, "n_sites": lat.n, "workload": WORKLOAD,
                           "reference": "GPU FP64 storage and arithmetic (equal to the FP64 oracle to rounding "
                                        "in the parity tests)"}))
+    elif args.split_kernels:
+        import torch
+        torch.cuda.set_device(0)
+        lat = tree_lattice(args.sites)
+        print(json.dumps({"split_kernels": split_kernels(lat, args.steps, torch), "n_sites": lat.n,
+                          "workload": workload_name(lat.n, 0.55)}))
     elif args.adjoint_only:
         import torch
         torch.cuda.set_device(0)

@@ -61,3 +61,24 @@ def root_midplane_objective(lattice, seed=11770, peak=0.02, spread=0.1) -> Objec
 def adjoint_case(target_sites=2_000_000, depth=4, seed=11770, n_sectors=8, n_rings=8):
     lat = tree_lattice(target_sites, depth=depth, seed=seed, n_sectors=n_sectors, n_rings=n_rings)
     return lat, root_midplane_objective(lat, seed=seed)
+
+
+def type_sorted(lattice):
+    """The same lattice with its sites reordered by site type (inner, wall,
+    inlet, outlet, inlet + wall, outlet + wall; (z, y, x) order within a type):
+    the layout of the paper's six collision-streaming kernels over type ranges
+    (Section 3.2.2).  Returns (lattice, [(type, first site, end)])."""
+    typ = np.asarray(lattice.type)
+    perm = np.argsort(typ, kind="stable")
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    src = lattice.src[:, perm]
+    src = np.where(src >= 0, inv[np.maximum(src, 0)], src).astype(np.int32)
+    out = geometry.from_arrays(lattice.xyz[perm], src, iolets=lattice.iolets, type=typ[perm],
+                               wall_normal=lattice.wall_normal[:, perm], amp_group=lattice.amp_group[perm])
+    ranges = []
+    for t in np.unique(typ):
+        idx = np.nonzero(typ[perm] == t)[0]
+        ranges.append((int(t), int(idx[0]), int(idx[-1]) + 1))
+    return out, ranges
+

@@ -105,3 +105,20 @@ def test_tile_sources_increase_and_fit_16_bits(depth, seed, sites):
         worst = max(worst, int((hi[has] - lo[has]).max()))
     assert worst <= 65533
     assert worst < 4 * T
+
+
+def test_type_sorted_lattice_is_a_relabelling():
+    """The site permutation of the per-type layout keeps every source at
+    x - c_i and every wall / iolet code, and groups the types in ranges."""
+    from paper_2202_11770_gb300 import workloads
+    lat = geo.tree(2, 2202, target_sites=30_000, length_ratio=5.0)
+    s, ranges = workloads.type_sorted(lat)
+    assert s.n == lat.n and sorted(map(tuple, s.xyz.tolist())) == sorted(map(tuple, lat.xyz.tolist()))
+    assert [b for _, b, _ in ranges][0] == 0 and ranges[-1][2] == lat.n
+    assert all(e == b2 for (_, _, e), (_, b2, _) in zip(ranges[:-1], ranges[1:]))
+    for t, b, e in ranges:
+        assert (s.type[b:e] == t).all()
+    for i in range(18):
+        m = s.src[i] >= 0
+        assert np.array_equal(s.xyz[s.src[i][m]], s.xyz[m] - geo.CI[i + 1])
+    assert np.array_equal(np.sort(s.src[s.src < 0]), np.sort(lat.src[lat.src < 0]))
