@@ -327,14 +327,34 @@ def adjoint_ratio(steps, torch, sites=2_000_000, full_index=False):
     e1.record(s.stream)
     torch.cuda.synchronize()
     adj = e0.elapsed_time(e1)
-    K = max(2, int(math.ceil(math.sqrt(steps))))  # the library's checkpoint interval: ceil(sqrt N), made even
-    K += K % 2
+    K = s.adjoint_plan(steps, obj.sites.size, ws[2])[0]
     out = {"workload": "seeded depth-4 tree, 64 inlet amplitude groups, FP32", "n_sites": lat.n, "steps": steps,
            "checkpoint_interval": K, "forward_ms": fwd, "adjoint_ms": adj,
            "ratio": adj / min(fwd.values()), "ratio_vs_pull_ab": adj / fwd["ab"],
            "J": J, "dJ_dtau": dtau, "probe_sites": int(obj.sites.size),
            "adjoint_workspace_gb": ws[2] / 1e9, "index": "compact" if s.compact_index else "int32"}
-    del s, ws
+    del ws
+    torch.cuda.empty_cache()
+    # the same run with most of the free device memory as workspace: whole
+    # segments of states are kept from the forward sweep, not recomputed
+    free = torch.cuda.mem_get_info()[0]
+    base = hemegb.hlb_adjoint_workspace_bytes(s._h, steps, obj.sites.size)
+    extra = max(0, int(0.6 * free) - base)
+    _, kept, rec, used = s.adjoint_plan(steps, obj.sites.size, base + extra)
+    if kept > 0:
+        ws = s.adjoint_workspace(steps, obj.sites.size, extra_bytes=used - base)
+        s.init_equilibrium()
+        torch.cuda.synchronize()
+        e0.record(s.stream)
+        J2, dtau2, damp2 = s.adjoint(steps, obj.sites, obj.target, obj.axis, workspace=ws)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        adj2 = e0.elapsed_time(e1)
+        out["memory"] = {"adjoint_ms": adj2, "ratio": adj2 / min(fwd.values()), "workspace_gb": used / 1e9,
+                         "kept_segments": kept, "recomputed_steps": rec,
+                         "identical": bool(J2 == J and dtau2 == dtau and np.array_equal(damp2, damp))}
+        del ws
+    del s
     torch.cuda.empty_cache()
     return out
 

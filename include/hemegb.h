@@ -273,6 +273,16 @@ int hlb_set_state(hlb_solver* h, const void* f, int32_t where, int64_t t);
  * (checkpoints + one segment of states + adjoint buffers). */
 int hlb_adjoint_workspace_bytes(const hlb_solver* h, int64_t nsteps, int64_t n_probe,
                                 size_t* bytes);
+/* A workspace larger than that minimum trades memory for recomputation: the
+ * run then keeps the post-collision states of whole checkpoint segments from
+ * its forward sweep (K more states each, K = 2 ceil(ceil(sqrt N) / 2) the
+ * checkpoint interval, every segment but the last) and recomputes only the
+ * others; results are identical.  hlb_adjoint_plan reports, for a workspace
+ * of ws_bytes, the interval K, the kept segments, the steps still recomputed
+ * and the bytes the run uses (any output may be NULL); HLB_ERR_WS below the
+ * minimum. */
+int hlb_adjoint_plan(const hlb_solver* h, int64_t nsteps, int64_t n_probe, size_t ws_bytes, int64_t* interval,
+                     int64_t* kept_segments, int64_t* recomputed_steps, size_t* bytes_used);
 int hlb_adjoint_run(hlb_solver* h, int64_t nsteps, const hlb_objective* obj, void* dev_ws,
                     size_t ws_bytes, double* J, double* dJ_dtau, double* dJ_damp);
 int hlb_n_amp_groups(const hlb_solver* h);

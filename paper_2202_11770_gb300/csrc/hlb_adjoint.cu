@@ -338,8 +338,8 @@ __device__ __forceinline__ typename Real<S>::type adjoint_iolet_site(const S* __
         h = ldpop(prev + (i == 0 ? x : (code >= 0 ? (int64_t)i * n + code : (int64_t)lane_opp(i) * n + x)));
         own = ldpop(prev + (int64_t)i * n + x);
       }
-      R d, jx, jy, jz;
-      warp_moment_sums<R>(own, i, &d, &jx, &jy, &jz);
+      R d, jx, jy, jz;  // summed in the forward's order: f(t) gets the forward's bits
+      lane_moment_sums<R>(own, R(1), &d, &jx, &jy, &jz);
       const R rp = R(1) + d;
       const R ux = jx / rp, uy = jy / rp, uz = jz / rp;
       if (code <= -2) {
@@ -456,13 +456,13 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2
               const int32_t* __restrict__ tbase, const uint32_t* __restrict__ imask,
               const LinkRec* __restrict__ links, const double* __restrict__ amp, const AdjParams ap,
               const ProbeMap pm, const int32_t* __restrict__ sites, int64_t nsites, unsigned n_iolet_blocks,
-              unsigned stride, double* __restrict__ part, double* __restrict__ dlink, int store) {
+              const BlockDiv stride, double* __restrict__ part, double* __restrict__ dlink, int store) {
   using R = typename Real<S>::type;
   __shared__ R neq[Q][BLOCK];
   __shared__ R sh[BLOCK / 32];
-  const unsigned b = blockIdx.x, j = b / stride;
+  const unsigned b = blockIdx.x, j = block_div(b, stride);
   R d;
-  if (b % stride == 0 && j < n_iolet_blocks) {
+  if (b == j * stride.d && j < n_iolet_blocks) {
     d = adjoint_iolet_site<S, GPREV>(prev, cur, mu_next, mu_out, src, links, amp, ap, pm, sites, nsites, dlink,
                                      store, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
   } else {
@@ -546,7 +546,7 @@ cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, co
   auto kernel = gprev ? pick(std::true_type{}) : pick(std::false_type{});
   kernel<<<grid, BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src, h->d_ctab,
                                  h->d_tbase, h->d_imask, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
-                                 h->n_iolet_sites, gi, stride, dtau_part, dlink, st_);
+                                 h->n_iolet_sites, gi, make_block_div(stride), dtau_part, dlink, st_);
   return cudaGetLastError();
 }
 
@@ -576,15 +576,22 @@ cudaError_t launch_probe_adj(const hlb_solver* h, const void* fin, int mode, int
   return cudaGetLastError();
 }
 
+// Workspace of one adjoint run.  The minimum (`total`) holds the sqrt(N)
+// checkpoints, one segment of states and the adjoint buffers.  A larger
+// workspace keeps, in `keep`, the post-collision states of `n_keep` whole
+// segments from the forward sweep, so that the reverse sweep need not
+// recompute them: segments [nck - 1 - n_keep, nck - 1) (never the last one,
+// which runs in the solver's own scheme so that the run ends exactly as N
+// plain steps would).
 struct AdjLayout {
-  int64_t K = 1, nck = 1, nseg = 2;
+  int64_t K = 1, nck = 1, nseg = 2, n_keep = 0;
   size_t ck = 0, seg = 0, mu = 0, dtau = 0, dlink = 0, sites = 0, target = 0, jp = 0, gbegin = 0, pmask = 0,
-         pbase = 0, out = 0, total = 0;
+         pbase = 0, out = 0, keep = 0, total = 0, used = 0;
 };
 
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-AdjLayout adj_layout(const hlb_solver* h, int64_t N, int64_t np) {
+AdjLayout adj_layout(const hlb_solver* h, int64_t N, int64_t np, size_t ws_bytes = 0) {
   AdjLayout y;
   // AA checkpoints are taken after odd steps, so the interval is even
   y.K = (int64_t)ceil(sqrt((double)N));
@@ -607,6 +614,10 @@ AdjLayout adj_layout(const hlb_solver* h, int64_t N, int64_t np) {
   y.pbase = off; off += al256(sizeof(int32_t) * (size_t)((h->n + 31) / 32));
   y.out = off; off += al256(sizeof(double) * (size_t)(2 + h->n_groups_total));
   y.total = off;
+  y.keep = off;
+  if (ws_bytes > y.total && y.nck > 1)
+    y.n_keep = std::min<int64_t>(y.nck - 1, (int64_t)((ws_bytes - y.total) / (st * (size_t)y.K)));
+  y.used = y.total + st * (size_t)y.K * (size_t)y.n_keep;
   return y;
 }
 
@@ -672,65 +683,90 @@ int run_adjoint(hlb_solver* h, int64_t N, const hlb_objective* obj, char* ws, co
   TRY(cudaMemcpyAsync(gbegin, h->group_link_begin.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, st));
   Probe pr{d_sites, d_target, obj->axis[0], obj->axis[1], obj->axis[2], 1.0 / (double)N, np};
 
-  // ---- forward sweep in the solver's own scheme (the faster one for the
-  // lattice size when it was created with AUTO).  Checkpoint 0 is f(t0) in
-  // natural layout; checkpoint c >= 1 is, for AA, f(cK) taken after an odd
-  // step (natural layout) and, for pull A-B, s'(cK - 1), from which the
-  // segment's first step gathers f(cK). ----
-  const int64_t K = y.K, nck = y.nck;
+  // ---- forward sweep, segment by segment.  A kept segment runs pull steps
+  // that write its post-collision states into its kept slots; every other
+  // segment runs the solver's own scheme (the faster one for the lattice size
+  // when it was created with AUTO).  Checkpoint c is taken at the start of
+  // segment c: f(cK) in natural layout (checkpoint 0, and after an AA odd
+  // step) or s'(cK - 1), from which the segment's first step gathers f(cK)
+  // (ckg[c]). ----
+  const int64_t K = y.K, nck = y.nck, A = nck - 1 - y.n_keep;  // kept: [A, nck - 1)
   const bool ab = h->scheme == HLB_PULL_AB;
+  auto kept = [&](int64_t c) { return c >= A && c < nck - 1; };
+  auto kp = [&](int64_t c, int64_t j) -> void* { return ws + y.keep + stb * (size_t)((c - A) * K + j); };
+  std::vector<char> ckg((size_t)nck, 0);
+  void* W = sg(0);                  // AA working buffer
+  const void* in = ck(0);           // pull: f(t) in place (gather false) or s'(t - 1)
+  bool gather = false, in_aa = false, swapped = false;
+  for (int64_t c = 0; c < nck; ++c) {
+    const int64_t sb = c * K, se = std::min<int64_t>(N, (c + 1) * K);
+    const bool aa_mode = !ab && !kept(c);
+    if (c > 0) {
+      TRY(cudaMemcpyAsync(ck(c), in_aa ? W : in, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+      ckg[(size_t)c] = in_aa ? 0 : 1;
+    }
+    if (aa_mode && !in_aa) {
+      // f(sb) in natural layout, with the boundary values the AA pass would have written
+      if (c == 0)
+        TRY(cudaMemcpyAsync(W, ck(0), h->state_bytes(), cudaMemcpyDeviceToDevice, st));
+      else
+        TRY(hlb_launch_state(h, in, HLB_READ_GATHER_AB, t0 + sb - 1, W, -1, st));
+      in_aa = true;
+      swapped = false;
+    } else if (!aa_mode && in_aa) {
+      in = W;  // f(sb) in place after an AA odd step (K is even)
+      gather = false;
+      in_aa = false;
+    }
+    for (int64_t s = sb; s < se; ++s) {
+      if (aa_mode) {
+        TRY(hlb_launch_aa(h, W, swapped, t0 + s, st));
+        swapped = !swapped;
+      } else {
+        // pull A-B: two working buffers (segment slots 0 and 1) or the kept
+        // slots; the final s'(t0 + N - 1) goes straight into the solver's
+        // buffer 0, free during the run (the start state is checkpoint 0)
+        void* out_ = kept(c) ? kp(c, s - sb) : (s == N - 1 ? h->f[0] : sg(s & 1));
+        TRY(hlb_launch_step(h, in, out_, gather, t0 + s - 1, st));
+        in = out_;
+        gather = true;
+      }
+    }
+  }
   int fin_mode;
-  if (ab) {
-    // two working buffers (segment slots 0 and 1); the final s'(t0 + N - 1)
-    // goes straight into the solver's buffer 0, which is free during the
-    // run (the start state was copied to checkpoint 0)
-    const void* in = ck(0);
-    bool gather = false;
-    for (int64_t s = 0; s < N; ++s) {
-      void* out_ = s == N - 1 ? h->f[0] : sg(s & 1);
-      TRY(hlb_launch_step(h, in, out_, gather, t0 + s - 1, st));
-      in = out_;
-      gather = true;
-      if ((s + 1) % K == 0 && (s + 1) / K < nck)
-        TRY(cudaMemcpyAsync(ck((s + 1) / K), out_, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
-    }
-    fin_mode = HLB_READ_GATHER_AB;
-  } else {
-    void* W = sg(0);
-    TRY(cudaMemcpyAsync(W, ck(0), h->state_bytes(), cudaMemcpyDeviceToDevice, st));
-    bool swapped = false;
-    for (int64_t s = 0; s < N; ++s) {
-      TRY(hlb_launch_aa(h, W, swapped, t0 + s, st));
-      swapped = !swapped;
-      if (!swapped && (s + 1) % K == 0 && (s + 1) / K < nck)
-        TRY(cudaMemcpyAsync(ck((s + 1) / K), W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
-    }
+  if (in_aa) {
     // the final state f(t0 + N) in the AA layout it ended in
     TRY(cudaMemcpyAsync(h->f[0], W, h->state_bytes(), cudaMemcpyDeviceToDevice, st));
     fin_mode = swapped ? HLB_READ_GATHER_AA : HLB_READ_LOCAL;
+  } else {
+    fin_mode = HLB_READ_GATHER_AB;
   }
   const void* fin_state = h->f[0];
 
   // ---- reverse: recompute each segment's post-collision states with the
-  // pull kernels from its checkpoint, then sweep it backwards ----
+  // pull kernels from its checkpoint (kept segments need none), then sweep
+  // it backwards ----
   int a = 0;  // mu[a] holds mu(t+1)
   TRY(cudaMemsetAsync(mu[a], 0, h->state_bytes(), st));
   TRY(launch_probe_adj<S>(h, fin_state, fin_mode, t0 + N - 1, pr, mu[a], jp, st));
   for (int64_t c = nck - 1; c >= 0; --c) {
     const int64_t sb = c * K, se = std::min<int64_t>(N, (c + 1) * K);
-    const bool ck_gather = ab && c > 0;  // checkpoint holds s'(cK - 1)
-    const void* rin = ck(c);
-    bool rg = ck_gather;
-    for (int64_t s = sb; s < se; ++s) {
-      TRY(hlb_launch_step(h, rin, sg(s - sb), rg, t0 + s - 1, st));
-      rin = sg(s - sb);
-      rg = true;
+    const bool ck_gather = ckg[(size_t)c] != 0;  // checkpoint holds s'(cK - 1)
+    auto slot = [&](int64_t j) -> void* { return kept(c) ? kp(c, j) : sg(j); };
+    if (!kept(c)) {
+      const void* rin = ck(c);
+      bool rg = ck_gather;
+      for (int64_t s = sb; s < se; ++s) {
+        TRY(hlb_launch_step(h, rin, sg(s - sb), rg, t0 + s - 1, st));
+        rin = sg(s - sb);
+        rg = true;
+      }
     }
     for (int64_t s = se - 1; s >= sb; --s) {
-      const void* prev = s == sb ? ck(c) : sg(s - sb - 1);
+      const void* prev = s == sb ? ck(c) : slot(s - sb - 1);
       const bool gprev = s != sb || ck_gather;  // f(s) gathered from s'(s - 1), or a checkpoint in place
       // mu(s) = C^T G^T mu(s+1) + dJ/df(s) at the probes (s >= 1), in one pass
-      TRY(launch_adjoint<S>(h, prev, gprev, sg(s - sb), mu[a], mu[a ^ 1], t0 + s - 1, t0 + s, pm, dtau_part, dlink,
+      TRY(launch_adjoint<S>(h, prev, gprev, slot(s - sb), mu[a], mu[a ^ 1], t0 + s - 1, t0 + s, pm, dtau_part, dlink,
                             s >= 1, st));
       a ^= 1;
     }
@@ -780,12 +816,26 @@ extern "C" int hlb_adjoint_workspace_bytes(const hlb_solver* h, int64_t nsteps, 
   return HLB_OK;
 }
 
+extern "C" int hlb_adjoint_plan(const hlb_solver* h, int64_t nsteps, int64_t n_probe, size_t ws_bytes,
+                                int64_t* interval, int64_t* kept_segments, int64_t* recomputed_steps,
+                                size_t* bytes_used) {
+  if (!h) return hlb_fail(HLB_ERR_ARG, "null solver");
+  if (nsteps < 1 || n_probe < 0) return hlb_fail(HLB_ERR_ARG, "nsteps must be >= 1 and n_probe >= 0");
+  const AdjLayout y = adj_layout(h, nsteps, n_probe, ws_bytes);
+  if (ws_bytes < y.total) return hlb_fail(HLB_ERR_WS, "workspace below the minimum of hlb_adjoint_workspace_bytes");
+  if (interval) *interval = y.K;
+  if (kept_segments) *kept_segments = y.n_keep;
+  if (recomputed_steps) *recomputed_steps = nsteps - y.n_keep * y.K;
+  if (bytes_used) *bytes_used = y.used;
+  return HLB_OK;
+}
+
 static int adjoint_run_impl(hlb_solver* h, int64_t nsteps, const hlb_objective* obj, void* ws, size_t ws_bytes,
                             double* J, double* dtau, double* damp) {
   int rc = check_objective(h, nsteps, obj);
   if (rc) return rc;
   if (h->any_wk()) return hlb_fail(HLB_ERR_ARG, "the adjoint does not differentiate Windkessel outlets");
-  AdjLayout y = adj_layout(h, nsteps, obj->n_probe);
+  AdjLayout y = adj_layout(h, nsteps, obj->n_probe, ws_bytes);
   if (!ws || ((uintptr_t)ws & 255)) return hlb_fail(HLB_ERR_WS, "adjoint workspace missing or not 256-byte aligned");
   if (ws_bytes < y.total)
     return hlb_fail(HLB_ERR_WS, "adjoint workspace too small: need " + std::to_string(y.total) + " bytes");

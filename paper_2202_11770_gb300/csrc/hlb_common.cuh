@@ -126,6 +126,31 @@ struct StepParams {
 };
 static_assert(MAX_IOLETS % 64 == 0, "coupling mask words");
 
+// Division of a block number b < 2^31 by a fixed divisor d without an
+// integer divide in the kernel: q = (b >> s) for d a power of two (m = 0),
+// else q = umulhi(b, m) >> s with l = ceil(log2 d), m = ceil(2^(31+l) / d),
+// s = l - 1, which is exact for all b < 2^31 (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994: m d lies in
+// [2^(31+l), 2^(31+l) + 2^l]).
+struct BlockDiv {
+  uint32_t d, m, s;
+};
+inline BlockDiv make_block_div(uint32_t d) {
+  BlockDiv r{d, 0u, 0u};
+  if ((d & (d - 1)) == 0) {
+    while ((1u << r.s) < d) ++r.s;
+    return r;
+  }
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;  // ceil(log2 d)
+  r.m = (uint32_t)((((uint64_t)1 << (31 + l)) + d - 1) / d);
+  r.s = l - 1;
+  return r;
+}
+__device__ __forceinline__ uint32_t block_div(uint32_t b, const BlockDiv& q) {
+  return q.m == 0 ? (b >> q.s) : (__umulhi(b, q.m) >> q.s);
+}
+
 // Relaxation rate 1/tau in the arithmetic type of a kernel.
 template <typename R> __device__ __forceinline__ R omega_of(const StepParams& p);
 template <> __device__ __forceinline__ float omega_of<float>(const StepParams& p) { return p.omegaf; }

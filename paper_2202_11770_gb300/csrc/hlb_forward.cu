@@ -161,12 +161,12 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
                                                 const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
                                                 const int32_t* __restrict__ tbase, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
-                                                int64_t nsites, unsigned n_iolet_blocks, unsigned stride,
+                                                int64_t nsites, unsigned n_iolet_blocks, const BlockDiv stride,
                                                 const uint32_t* __restrict__ imask, uint32_t pf, uint32_t tile0,
                                                 const StepParams p) {
   using R = typename Real<S>::type;
-  const unsigned b = blockIdx.x, j = b / stride;
-  if (b % stride == 0 && j < n_iolet_blocks) {
+  const unsigned b = blockIdx.x, j = block_div(b, stride);
+  if (b == j * stride.d && j < n_iolet_blocks) {
     pdl_wait();
     pdl_trigger();
     step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
@@ -341,10 +341,11 @@ __device__ __forceinline__ R iolet_value(int i, const LinkRec& L, R out, R rho, 
 // site's number of iolet links.  The site's stored post-collision populations
 // s'_ibar(x) sit in slot i of x after an even step, and in the slot it read
 // direction i from after an odd step; an iolet link's slot is slot i of x in
-// both cases.  Boundary values use the moments of these stored values (summed
-// in direction order, as the per-thread read-back code does), as the A-B
-// gather does.  icode[q][i - 1] is the index code of direction i at iolet
-// site q: 72 contiguous bytes a site.
+// both cases.  Boundary values use the moments of these stored values, as
+// the A-B gather does; lane i first takes s'_i(x) from lane ibar, so that the
+// sums run over s'_0, s'_1, ... in the order of the A-B warp path and the two
+// schemes give the same bits.  icode[q][i - 1] is the index code of direction
+// i at iolet site q: 72 contiguous bytes a site.
 template <typename S, bool ODD>
 __global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict__ icode,
                                                 const LinkRec* __restrict__ links, const double* __restrict__ amp,
@@ -365,8 +366,8 @@ __global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict_
   const int64_t n = p.n;
   R v = R(0);  // s'_ibar(x), the value in the slot the link of direction i reads
   if (i < Q) v = to_real(A[i == 0 ? x : (ODD ? aa_addr(i, code, n, x) : (int64_t)i * n + x)]);
-  R d, jx, jy, jz;  // rho = 1 + sum v, j = -sum v_k c_k, in direction order
-  lane_moment_sums<R>(v, R(-1), &d, &jx, &jy, &jz);
+  R d, jx, jy, jz;  // rho = 1 + sum s'_k, j = sum s'_k c_k, in direction order
+  lane_moment_sums<R>(__shfl_sync(FULL_MASK, v, i < Q ? lane_opp(i) : i), R(1), &d, &jx, &jy, &jz);
   const R rho = R(1) + d;
   const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
   if (code > -2) return;
@@ -710,7 +711,7 @@ cudaError_t launch_gather(const hlb_solver* h, const void* fin, void* fout, cons
   auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
                            : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
   return launch_pdl(kernel, grid, BLOCK, s, (const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase, h->d_links,
-                    h->d_amp, h->d_iolet_sites, h->n_iolet_sites, gi, gi ? grid / gi : 1, h->d_imask,
+                    h->d_amp, h->d_iolet_sites, h->n_iolet_sites, gi, make_block_div(gi ? grid / gi : 1), h->d_imask,
                     (uint32_t)h->n_sm * 5u, tile0, p);
 }
 

@@ -92,6 +92,8 @@ _PROTOS = {
     "hlb_get_state": (C.c_int, [_P, _P, C.c_int32, C.POINTER(C.c_int64)]),
     "hlb_set_state": (C.c_int, [_P, _P, C.c_int32, C.c_int64]),
     "hlb_adjoint_workspace_bytes": (C.c_int, [_P, C.c_int64, C.c_int64, C.POINTER(C.c_size_t)]),
+    "hlb_adjoint_plan": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_size_t, C.POINTER(C.c_int64),
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
     "hlb_adjoint_run": (C.c_int, [_P, C.c_int64, C.POINTER(hlb_objective), _P, C.c_size_t,
                                   C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "hlb_mass_static": (C.c_int, [_P, C.c_int32, C.c_int64, _P, _P]),
@@ -378,11 +380,21 @@ class Solver:
         assert f.nbytes == 19 * self.n * _ELEM[self.precision]
         _check(self._lib.hlb_set_state(self._h, _P(f.ctypes.data), HLB_HOST, int(t)))
 
-    def adjoint_workspace(self, nsteps, n_probe):
-        """A device workspace (uint8 tensor, 256-byte aligned pointer) for adjoint()."""
-        nb = hlb_adjoint_workspace_bytes(self._h, nsteps, n_probe)
+    def adjoint_workspace(self, nsteps, n_probe, extra_bytes=0):
+        """A device workspace (uint8 tensor, 256-byte aligned pointer, size) for
+        adjoint(): the sqrt(N)-checkpoint minimum, plus ``extra_bytes`` in which
+        the run keeps whole segments of states instead of recomputing them."""
+        nb = hlb_adjoint_workspace_bytes(self._h, nsteps, n_probe) + int(extra_bytes)
         ws = self._torch.empty(nb + 256, dtype=self._torch.uint8, device="cuda")
         return ws, (ws.data_ptr() + 255) & ~255, nb
+
+    def adjoint_plan(self, nsteps, n_probe, ws_bytes):
+        """(checkpoint interval K, kept segments, recomputed steps, bytes used)
+        of an adjoint run with a workspace of ``ws_bytes``."""
+        k, kept, rec, used = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
+        _check(self._lib.hlb_adjoint_plan(self._h, int(nsteps), int(n_probe), int(ws_bytes), C.byref(k),
+                                          C.byref(kept), C.byref(rec), C.byref(used)))
+        return k.value, kept.value, rec.value, used.value
 
     def adjoint(self, nsteps, sites, target, axis, workspace=None):
         """(J, dJ/dtau, dJ/da[groups]) over nsteps from the current state.

@@ -133,3 +133,40 @@ def test_adjoint_leaves_the_forward_state(scheme):
     assert ta == tb == N
     assert fa.tobytes() == fb.tobytes() and ga.tobytes() == gb.tobytes()
     assert ma == mb and np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("precision,scheme", [("fp32", "aa"), ("fp32", "ab"), ("fp64", "aa")])
+def test_kept_segments_give_identical_results(precision, scheme):
+    """A larger workspace keeps whole segments of post-collision states from
+    the forward sweep instead of recomputing them: the gradients, J and the
+    final state are bit-identical to the sqrt(N)-memory run, whether none,
+    some or all but the last segment are kept."""
+    lat = geo.tree(1, 7, root_radius=4.0, length_ratio=5.0, n_sectors=2, n_rings=2)
+    N = 41                                   # K = 8, six segments, the last one short and odd
+    probe = np.nonzero(lat.xyz[:, 2] == int(lat.info["root_length"] // 2))[0]
+    target = np.full(probe.size, 0.02)
+    amps = np.array([1.0, 0.9, 1.1, 0.95])
+    s = hemegb.Solver(lat, tau=0.7, precision=precision, scheme=scheme)
+    base = hemegb.hlb_adjoint_workspace_bytes(s._h, N, probe.size)
+    K, kept_all, rec_all, used_all = s.adjoint_plan(N, probe.size, 1 << 40)
+    assert K == 8 and kept_all == 5 and rec_all == N - 5 * K
+    per_seg = (used_all - base) // kept_all
+    assert per_seg * kept_all == used_all - base and per_seg >= 19 * lat.n * K * (4 if precision == "fp32" else 8)
+    assert s.adjoint_plan(N, probe.size, base)[1:] == (0, N, base)
+    with pytest.raises(hemegb.HlbError):
+        s.adjoint_plan(N, probe.size, base - 1)
+    runs = []
+    for n_keep in (0, 2, 5):
+        s = hemegb.Solver(lat, tau=0.7, precision=precision, scheme=scheme)
+        _setup(s, lat, amps)
+        s.step(3)                            # start mid AA cycle
+        ws = s.adjoint_workspace(N, probe.size, extra_bytes=n_keep * per_seg + per_seg // 2)
+        assert s.adjoint_plan(N, probe.size, ws[2])[1] == n_keep
+        J, dtau, damp = s.adjoint(N, probe, target, [0, 0, 1], workspace=ws)
+        f, t = s.state()
+        s.step(4)
+        runs.append((J, dtau, np.asarray(damp), f, t, s.state()[0]))
+    for r in runs[1:]:
+        assert r[0] == runs[0][0] and r[1] == runs[0][1] and r[2].tobytes() == runs[0][2].tobytes()
+        assert r[3].tobytes() == runs[0][3].tobytes() and r[4] == runs[0][4] == N + 3
+        assert r[5].tobytes() == runs[0][5].tobytes()
