@@ -19,8 +19,9 @@ than L2, so no flush is needed between steps.
 updates over the slowest rank's time.
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure, plain C,
-sites split over all host cores) on the same lattice: a bounded number of
-full-lattice steps.  The default run also reports the oracle at one thread,
+sites split over all host cores) for the same --warmup and --steps, on the
+same lattice, or on a smaller tree of the same generator when the full one
+would not finish within --ref-budget seconds.  The default run also reports the oracle at one thread,
 and checks every storage form's velocity and wall shear stress against the
 oracle on a 1M-site tree after 1,000 steps (``precision_vs_oracle``).
 """
@@ -536,29 +537,53 @@ def precision_vs_oracle(sites, steps, torch, forms=(("fp32", "ab"), ("fp32", "aa
 
 # ---------------------------------------------------------------------------
 def run_reference(args):
+    """The oracle arm: exactly `--warmup` W untimed and `--steps` K timed
+    oracle steps, sites split over all host cores.  One full-lattice step is
+    timed first (it counts as the first warm-up step); when W + K full steps
+    would take longer than --ref-budget seconds, every step instead runs on a
+    smaller tree from the same seeded generator, sized to fit that budget
+    (the sample is named in the line)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    lat = tree_lattice(args.sites)
-    w = min(args.warmup, 1)
-    k = max(1, min(args.steps, args.ref_steps))
-    cores = host_cores()
     import oracle
-    o = oracle.Oracle(lat, tau=0.55, threads=cores)
-    set_bc(o, lat)
-    o.init_equilibrium()
-    o.step(w)
+    cores = host_cores()
+    lat = tree_lattice(args.sites)
+    n_full = lat.n
+    w, k = max(args.warmup, 1), max(args.steps, 1)
+
+    def oracle_on(lattice):
+        o = oracle.Oracle(lattice, tau=0.55, threads=cores)
+        set_bc(o, lattice)
+        o.init_equilibrium()
+        return o
+
+    o = oracle_on(lat)
+    t0 = time.perf_counter()
+    o.step(1)
+    t_full = time.perf_counter() - t0
+    done = 1
+    full = (w + k) * t_full <= args.ref_budget
+    if not full:
+        target = max(1_000_000, int(lat.n * args.ref_budget / ((w + k) * t_full)))
+        del o
+        lat = tree_lattice(target)
+        o = oracle_on(lat)
+        done = 0
+    o.step(w - done)
     t0 = time.perf_counter()
     o.step(k)
     dt = time.perf_counter() - t0
     v = lat.n * k / dt / 1e6
-    sample = (f"{k} full-lattice steps of the {lat.n}-site tree after {w} warm-up step(s), FP64 oracle "
-              f"on {cores} threads")
+    sample = (f"{k} steps after {w} warm-up step(s) of the {lat.n}-site seeded tree"
+              + ("" if full else f" (a smaller tree of the same generator: {w + k} full steps of the "
+                                 f"{args.sites // 1_000_000}M-site tree would take {(w + k) * t_full:.0f} s)")
+              + f", FP64 oracle on {cores} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": k, "warmup": w, "ms_per_step": dt / k * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_sites": lat.n},
+        "config": {"workload": workload_name(n_full, 0.55), "n_sites": n_full, "tau": 0.55},
         "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -687,7 +712,8 @@ def main():
                     help="the paper's per-site-type kernels on streams against the fused kernel (FP32 pull A-B)")
     ap.add_argument("--precision-study", action="store_true",
                     help="u and WSS error of FP32/BF16/FP16 storage vs FP64 at 1k, 5k, 10k steps")
-    ap.add_argument("--ref-steps", type=int, default=3)
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="seconds the oracle arm may spend on its warm-up and timed steps")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="one form only, no e2e (profiling runs)")
     ap.add_argument("--tau", type=float, default=0.55, help="relaxation time of the timed headline form")
