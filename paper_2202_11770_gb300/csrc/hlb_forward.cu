@@ -129,20 +129,20 @@ __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __
   const bool dir = i < Q;
   const int64_t n = p.n, x = sites[w];
   const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
+  // the link record and amplitude load beside the populations, not after
+  // them (record 0 exists whenever a site has an iolet link)
+  const LinkRec L = links[code <= -2 ? -code - 2 : 0];
   R h = R(0), own = R(0);
   if (dir) {
     h = ldpop(fin + (i == 0 ? x : (code >= 0 ? (int64_t)i * n + code : (int64_t)lane_opp(i) * n + x)));
     own = ldpop(fin + (int64_t)i * n + x);
   }
+  const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
   R d, jx, jy, jz;
   lane_moment_sums<R>(own, R(1), &d, &jx, &jy, &jz);
   const R rho_s = R(1) + d;
   const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
-  if (code <= -2) {
-    const LinkRec L = links[-code - 2];
-    const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
-    h = lane_iolet_value<R>(i, L, h, rho_s, ux, uy, uz, a, p);
-  }
+  if (code <= -2) h = lane_iolet_value<R>(i, L, h, rho_s, ux, uy, uz, a, p);
   h = lane_collide<R>(h, i, omega_of<R>(p));
   if (dir) stpop<S>(fout + (int64_t)i * n + x, h);
 }
@@ -310,6 +310,126 @@ __global__ void __launch_bounds__(BLOCK, 4) k_aa_even2(S* A, const StepParams p)
   for (int i = 0; i < Q; ++i) __stcs(A2 + (int64_t)opp(i) * n2 + x2, P::from(h[i].x, h[i].y));
 }
 
+// collide_emit() of two sites at once, h[i] = (site x, site x + 1): the same
+// operations in the same order, each pair of scalar operations one paired
+// FP32 instruction (rounded as the scalar one), so each site gets the bits
+// of the per-thread collision.
+__device__ __forceinline__ float2 p_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 p_cdotu(int i, float2 ux, float2 uy, float2 uz) {
+  float2 s = p_splat(0.f);
+  if (cx(i)) s = p_add(s, cx(i) > 0 ? ux : p_neg(ux));
+  if (cy(i)) s = p_add(s, cy(i) > 0 ? uy : p_neg(uy));
+  if (cz(i)) s = p_add(s, cz(i) > 0 ? uz : p_neg(uz));
+  return s;
+}
+template <typename Emit>
+__device__ __forceinline__ void collide_pair(const float2* h, float omega, Emit&& emit) {
+  float2 drho = h[0], jx = p_splat(0.f), jy = p_splat(0.f), jz = p_splat(0.f);
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const int i = 2 * p + 1;
+    const float2 sp = p_add(h[i], h[i + 1]), dp = p_sub(h[i], h[i + 1]);
+    drho = p_add(drho, sp);
+    if (cx(i)) jx = cx(i) > 0 ? p_add(jx, dp) : p_sub(jx, dp);
+    if (cy(i)) jy = cy(i) > 0 ? p_add(jy, dp) : p_sub(jy, dp);
+    if (cz(i)) jz = cz(i) > 0 ? p_add(jz, dp) : p_sub(jz, dp);
+  }
+  const float2 rho = p_add(p_splat(1.f), drho);
+  const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+  const float2 ux = p_mul(jx, inv), uy = p_mul(jy, inv), uz = p_mul(jz, inv);
+  const float2 usq15 = p_mul(p_splat(1.5f), p_fma(uz, uz, p_fma(uy, uy, p_mul(ux, ux))));
+  const float2 om1 = p_splat(1.f - omega);
+  float2 wr[3], wd[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float ow = omega * wgt<float>(c == 0 ? 0 : (c == 1 ? 1 : 7));
+    wr[c] = p_mul(p_splat(ow), rho);
+    wd[c] = p_mul(p_splat(ow), drho);
+  }
+  emit(0, p_fma(om1, h[0], p_fma(p_neg(wr[0]), usq15, wd[0])));
+#pragma unroll
+  for (int p = 0; p < 9; ++p) {
+    const int i = 2 * p + 1, c = i <= 6 ? 1 : 2;
+    const float2 cu = p_cdotu(i, ux, uy, uz);
+    const float2 a = p_fma(p_mul(p_splat(4.5f), cu), cu, p_neg(usq15));
+    emit(i, p_fma(om1, h[i], p_fma(wr[c], p_fma(p_splat(3.f), cu, a), wd[c])));
+    emit(i + 1, p_fma(om1, h[i + 1], p_fma(wr[c], p_fma(p_splat(-3.f), cu, a), wd[c])));
+  }
+}
+
+// Pull A-B step (k_step) for 16-bit storage with two neighbouring sites x, x
+// + 1 per thread (n even, compact table, 32-bit offsets): the index words of
+// both in one 8-byte load per row, the two collisions in paired FP32
+// instructions (collide_pair: the bits of k_step) and 4-byte stores of the
+// pair; the gathers stay one per site and direction.  A block takes two
+// tiles.  A pair with one iolet site stores only its other site.  Three
+// blocks per SM (80 registers) measured 6 % faster than k_step on BF16 and
+// FP16 (issue-bound there), four (64 registers, with spills) 8 % slower.
+template <typename S>
+__global__ void __launch_bounds__(BLOCK, 3) k_step2(const S* __restrict__ fin, S* __restrict__ fout,
+                                                 const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
+                                                 const int32_t* __restrict__ tbase, const LinkRec* __restrict__ links,
+                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
+                                                 int64_t nsites, unsigned n_iolet_blocks, const BlockDiv stride,
+                                                 const uint32_t* __restrict__ imask, uint32_t pf,
+                                                 const StepParams p) {
+  using P = Pair<S>;
+  using T = typename P::T;
+  const unsigned b = blockIdx.x, j = block_div(b, stride);
+  if (b == j * stride.d && j < n_iolet_blocks) {
+    pdl_wait();
+    pdl_trigger();
+    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
+    return;
+  }
+  const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
+  const uint32_t k = b - min(n_iolet_blocks, j + 1);  // bulk block: tiles 2k, 2k + 1
+  const uint32_t x = 2 * (k * BLOCK + threadIdx.x);
+  const uint32_t tile = x / CT_TILE;
+  if (pf && threadIdx.x < 64) prefetch_tile<S, false, false>(fin, ctab, tbase, n, sn, 2 * (k + pf) + (threadIdx.x >> 5));
+  uint32_t m = 3u;  // bit 0: x is stepped elsewhere (iolet warps, or x >= n), bit 1: x + 1
+  uint32_t off[2][Q];
+  if (x < n) {
+    m = (__ldg(imask + (x >> 5)) >> (x & 31)) & 3u;  // x even: both bits in one word
+    uint2 w[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) w[q] = __ldcs(reinterpret_cast<const uint2*>(ctab + (uint32_t)q * sn + x));
+    const int4* tb = reinterpret_cast<const int4*>(tbase + (uint64_t)tile * CT_BASES);
+    int bs[20];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int4 v = __ldg(tb + q);
+      bs[4 * q] = v.x;
+      bs[4 * q + 1] = v.y;
+      bs[4 * q + 2] = v.z;
+      bs[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t wa = w[(i - 1) >> 1].x, wb = w[(i - 1) >> 1].y;
+      const uint32_t oa = (i & 1) ? (wa & 0xffffu) : (wa >> 16), ob = (i & 1) ? (wb & 0xffffu) : (wb >> 16);
+      off[0][i] = oa < CT_IOLET ? (uint32_t)i * n + (uint32_t)bs[i - 1] + oa : (uint32_t)opp(i) * n + x;
+      off[1][i] = ob < CT_IOLET ? (uint32_t)i * n + (uint32_t)bs[i - 1] + ob : (uint32_t)opp(i) * n + x + 1;
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (m == 3u) return;
+  const T* fin2 = reinterpret_cast<const T*>(fin);
+  float2 h[Q];
+  h[0] = P::to(__ldg(fin2 + x / 2));
+#pragma unroll
+  for (int i = 1; i < Q; ++i) h[i] = make_float2(ldpop(fin + off[0][i]), ldpop(fin + off[1][i]));
+  if (m == 0u) {
+    T* fout2 = reinterpret_cast<T*>(fout);
+    collide_pair(h, p.omegaf, [&](int i, float2 v) { __stcs(fout2 + ((uint32_t)i * n + x) / 2, P::from(v.x, v.y)); });
+  } else {
+    const uint32_t y = m == 1u ? x + 1 : x;  // the pair's site without iolet links
+    collide_pair(h, p.omegaf,
+                 [&](int i, float2 v) { stpop<S>(fout + (uint32_t)i * n + y, m == 1u ? v.y : v.x); });
+  }
+}
+
 // Boundary value of iolet link (pull direction i, record L) at a site whose
 // pre-collision moments at time t are (drho, u) and whose outgoing
 // post-collision population is `out` (= s'_ibar): incoming f_i(t+1) - w_i.
@@ -360,6 +480,10 @@ __global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict_
     x = __ldg(sites + q);
     if (i >= 1 && i < Q) code = __ldg(icode + q * (Q - 1) + (i - 1));
   }
+  // link record and amplitude do not change between steps: loaded before
+  // the wait for the step kernel (record 0 exists whenever there are iolet sites)
+  const LinkRec L = links[code <= -2 ? -code - 2 : 0];
+  const R a = q < nsites ? BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0) : R(0);
   pdl_wait();
   pdl_trigger();
   if (q >= nsites) return;  // uniform across the warp
@@ -371,8 +495,6 @@ __global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict_
   const R rho = R(1) + d;
   const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
   if (code > -2) return;
-  const LinkRec L = links[-code - 2];
-  const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
   const R val = lane_iolet_value<R>(i, L, v, rho, ux, uy, uz, a, p);
   lflux[-code - 2] = (double)val - (double)v;
   A[(int64_t)i * n + x] = from_real<S>(val);
@@ -708,6 +830,14 @@ cudaError_t launch_gather(const hlb_solver* h, const void* fin, void* fout, cons
   const unsigned gi = iolets ? (unsigned)((h->n_iolet_sites + 7) / 8) : 0u;  // 8 warps (sites) per block
   const unsigned grid = gi + ntiles;
   if (grid == 0) return cudaSuccess;
+  if constexpr (sizeof(S) == 2) {
+    if (h->compact && h->off32 && h->n % 2 == 0 && tile0 == 0 && ntiles == grid_for(h->n)) {
+      const unsigned g2 = gi + (unsigned)((h->n + 2 * BLOCK - 1) / (2 * BLOCK));
+      return launch_pdl(k_step2<S>, g2, BLOCK, s, (const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase,
+                        h->d_links, h->d_amp, h->d_iolet_sites, h->n_iolet_sites, gi,
+                        make_block_div(gi ? g2 / gi : 1), h->d_imask, (uint32_t)h->n_sm * 4u, p);
+    }
+  }
   auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)
                            : (h->off32 ? k_step<S, false, false> : k_step<S, true, false>);
   return launch_pdl(kernel, grid, BLOCK, s, (const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase, h->d_links,

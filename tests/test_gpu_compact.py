@@ -5,6 +5,11 @@ the gathered sources are the same, so every result must be bit-identical to
 the run on the int32 table (which the other GPU tests pin to the oracle).
 A tile whose sources of one direction span more than 65,533 sites cannot be
 encoded: the library then uses the int32 table.
+
+For 16-bit storage with an even number of sites the pull step on the compact
+table takes two sites a thread (paired loads, stores and collisions); its
+collisions are the per-thread operations in paired instructions, so it too
+gives the bits of the int32-table kernel.
 """
 import numpy as np
 import pytest
@@ -96,3 +101,24 @@ def test_largest_encodable_span(scheme, span, compact):
         s.step(4)
         out.append(s.state()[0])
     assert out[0].tobytes() == out[1].tobytes()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_two_site_pull_step_bit_identical(prec):
+    """Even site count (49,986, ragged last tile pair): the two-site pull kernel
+    on the compact table against the one-site kernels (int32 table, and the
+    large-lattice offsets), including pairs that hold one iolet site."""
+    lat = geo.tree(2, 2202, target_sites=50_009, length_ratio=5.0)
+    assert lat.n % 2 == 0 and lat.n % 512
+    isite = (lat.src <= -2).any(axis=0)
+    assert (isite[0::2] != isite[1::2]).any()
+    out = []
+    for full, wide in ((False, False), (True, False), (False, True)):
+        s = hemegb.Solver(lat, tau=0.55, precision=prec, scheme="ab", full_index=full, wide_offsets=wide)
+        _bc(s, lat)
+        s.init_equilibrium()
+        s.step(9)
+        out.append((s.state()[0], s.reduce()))
+    for f, (m, q) in out[1:]:
+        assert f.tobytes() == out[0][0].tobytes()
+        assert m == out[0][1][0] and np.array_equal(q, out[0][1][1])
