@@ -223,16 +223,18 @@ def time_form(lat, precision, scheme, steps, warmup, torch, dist=None, tau=0.55,
     return total, durs, t_first, compact
 
 
-def kernel_names(n):
-    """Names of the step kernels the library launches (pull A-B, AA odd step)."""
-    return ("k_step", "k_aa_odd")
+def kernel_names(n, compact=True, wide=False):
+    """Names of the step kernels the library launches (pull A-B, AA odd step):
+    the pull step takes two sites a thread (k_step2) on the compact table
+    with 32-bit offsets when the site count is even."""
+    return ("k_step2" if compact and not wide and n % 2 == 0 else "k_step", "k_aa_odd")
 
 
 def form_stats(lat, precision, scheme, total, durs, t_first, steps, peak, compact):
     """MLUPS, algorithmic GB/s and per-kernel rooflines of one timed form
     (CUDA events around every step: each step is one kernel launch)."""
     n = lat.n
-    k_ab, k_odd = kernel_names(n)
+    k_ab, k_odd = kernel_names(n, compact)
     e = ELEM[precision]
     out = {"scheme": scheme, "mlups": n * steps / (total * 1e-3) / 1e6, "ms_per_step": total / steps,
            "index": "compact" if compact else "int32"}
@@ -619,7 +621,7 @@ def run_ours(args):
     ms, total_updates = aggregate_ranks(ms, n * args.steps, dist, "cuda")
     value = total_updates / (ms * 1e-3) / 1e6
     head = form_stats(lat, prec0, scheme, ms, durs, t_first, args.steps, peak, compact)
-    kname = kernel_names(n)[0 if scheme == "ab" else 1]
+    kname = kernel_names(n, compact, args.wide_offsets)[0 if scheme == "ab" else 1]
     kst = head["kernels"][kname]
     traffic = None
     if (TRAFFIC["sha"] == kernel_sha() and TRAFFIC["index"] == ("compact" if compact else "int32")

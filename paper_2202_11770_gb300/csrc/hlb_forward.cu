@@ -242,6 +242,11 @@ template <> struct Pair<__half> {
   static __device__ __forceinline__ float2 to(T v) { return __half22float2(v); }
   static __device__ __forceinline__ T from(float a, float b) { return __floats2half2_rn(a, b); }
 };
+template <> struct Pair<float> {
+  using T = float2;
+  static __device__ __forceinline__ float2 to(T v) { return v; }
+  static __device__ __forceinline__ T from(float a, float b) { return make_float2(a, b); }
+};
 
 // Paired FP32 arithmetic (sm_100 and later): one instruction applies the
 // operation to .x and .y, each rounded as the scalar operation is.
@@ -357,14 +362,16 @@ __device__ __forceinline__ void collide_pair(const float2* h, float omega, Emit&
   }
 }
 
-// Pull A-B step (k_step) for 16-bit storage with two neighbouring sites x, x
-// + 1 per thread (n even, compact table, 32-bit offsets): the index words of
-// both in one 8-byte load per row, the two collisions in paired FP32
-// instructions (collide_pair: the bits of k_step) and 4-byte stores of the
-// pair; the gathers stay one per site and direction.  A block takes two
-// tiles.  A pair with one iolet site stores only its other site.  Three
-// blocks per SM (80 registers) measured 6 % faster than k_step on BF16 and
-// FP16 (issue-bound there), four (64 registers, with spills) 8 % slower.
+// Pull A-B step (k_step) with two neighbouring sites x, x + 1 per thread (n
+// even, compact table, 32-bit offsets; FP32 or 16-bit storage): the index
+// words of both in one 8-byte load per row, the two collisions in paired
+// FP32 instructions (collide_pair: the bits of k_step) and one store of the
+// pair per direction; the gathers stay one per site and direction.  A block
+// takes two tiles.  A pair with one iolet site stores only its other site.
+// Three blocks per SM (80 registers), on the 20M-site tree: BF16 447 -> 419
+// us (four blocks, 64 registers with spills: 485 us), FP32 577 -> 567 us.
+// The same pairing in the AA odd step, whose stores scatter, was slower
+// (463 -> 563 us BF16).
 template <typename S>
 __global__ void __launch_bounds__(BLOCK, 3) k_step2(const S* __restrict__ fin, S* __restrict__ fout,
                                                  const int32_t* __restrict__ src, const uint32_t* __restrict__ ctab,
@@ -830,12 +837,12 @@ cudaError_t launch_gather(const hlb_solver* h, const void* fin, void* fout, cons
   const unsigned gi = iolets ? (unsigned)((h->n_iolet_sites + 7) / 8) : 0u;  // 8 warps (sites) per block
   const unsigned grid = gi + ntiles;
   if (grid == 0) return cudaSuccess;
-  if constexpr (sizeof(S) == 2) {
+  if constexpr (sizeof(S) <= 4) {
     if (h->compact && h->off32 && h->n % 2 == 0 && tile0 == 0 && ntiles == grid_for(h->n)) {
       const unsigned g2 = gi + (unsigned)((h->n + 2 * BLOCK - 1) / (2 * BLOCK));
       return launch_pdl(k_step2<S>, g2, BLOCK, s, (const S*)fin, (S*)fout, h->d_src, h->d_ctab, h->d_tbase,
                         h->d_links, h->d_amp, h->d_iolet_sites, h->n_iolet_sites, gi,
-                        make_block_div(gi ? g2 / gi : 1), h->d_imask, (uint32_t)h->n_sm * 4u, p);
+                        make_block_div(gi ? g2 / gi : 1), h->d_imask, (uint32_t)h->n_sm * 3u, p);
     }
   }
   auto kernel = h->compact ? (h->off32 ? k_step<S, false, true> : k_step<S, true, true>)

@@ -47,3 +47,12 @@ def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
     assert bench.kernel_sha() == h0
     f.write_text(code.replace("1.f", "2.f"))
     assert bench.kernel_sha() != h0
+
+
+def test_kernel_names_follow_the_launch_rule():
+    # the pull step takes two sites a thread on the compact table with 32-bit
+    # offsets when the site count is even
+    assert bench.kernel_names(20_000_864) == ("k_step2", "k_aa_odd")
+    assert bench.kernel_names(20_000_865)[0] == "k_step"
+    assert bench.kernel_names(20_000_864, compact=False)[0] == "k_step"
+    assert bench.kernel_names(20_000_864, wide=True)[0] == "k_step"

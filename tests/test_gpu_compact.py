@@ -6,10 +6,10 @@ the run on the int32 table (which the other GPU tests pin to the oracle).
 A tile whose sources of one direction span more than 65,533 sites cannot be
 encoded: the library then uses the int32 table.
 
-For 16-bit storage with an even number of sites the pull step on the compact
-table takes two sites a thread (paired loads, stores and collisions); its
-collisions are the per-thread operations in paired instructions, so it too
-gives the bits of the int32-table kernel.
+With an even number of sites the pull step on the compact table takes two
+sites a thread (paired index loads, stores and collisions); the collisions
+are the per-thread operations in paired instructions, so it too gives the
+bits of the int32-table kernel.
 """
 import numpy as np
 import pytest
@@ -103,18 +103,20 @@ def test_largest_encodable_span(scheme, span, compact):
     assert out[0].tobytes() == out[1].tobytes()
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_two_site_pull_step_bit_identical(prec):
-    """Even site count (49,986, ragged last tile pair): the two-site pull kernel
-    on the compact table against the one-site kernels (int32 table, and the
-    large-lattice offsets), including pairs that hold one iolet site."""
+@pytest.mark.parametrize("prec,scheme", [("fp32", "ab"), ("bf16", "ab"), ("fp16", "ab"), ("bf16", "aa"),
+                                         ("fp16", "aa")])
+def test_two_site_kernels_bit_identical(prec, scheme):
+    """Even site count (49,986, ragged last tile pair): the two-site pull
+    kernel on the compact table against the one-site kernels (int32 table,
+    and the large-lattice offsets), including pairs that hold one iolet
+    site; and the AA kernels at an even site count (two-site even step)."""
     lat = geo.tree(2, 2202, target_sites=50_009, length_ratio=5.0)
     assert lat.n % 2 == 0 and lat.n % 512
     isite = (lat.src <= -2).any(axis=0)
     assert (isite[0::2] != isite[1::2]).any()
     out = []
     for full, wide in ((False, False), (True, False), (False, True)):
-        s = hemegb.Solver(lat, tau=0.55, precision=prec, scheme="ab", full_index=full, wide_offsets=wide)
+        s = hemegb.Solver(lat, tau=0.55, precision=prec, scheme=scheme, full_index=full, wide_offsets=wide)
         _bc(s, lat)
         s.init_equilibrium()
         s.step(9)
