@@ -296,7 +296,7 @@ def e2e_job(lat, steps, torch):
     return n * steps / dt / 1e6, h2d_step, d2h_step, t_create, dt
 
 
-def adjoint_ratio(steps, torch, sites=2_000_000, full_index=False):
+def adjoint_ratio(steps, torch, sites=2_000_000, full_index=False, memory=True):
     """Adjoint (forward with sqrt(N) checkpoints + recompute + reverse) vs
     forward-only time over the same N steps: seeded depth-4 tree, ~2M sites,
     64 inlet amplitude groups, FP32."""
@@ -344,7 +344,7 @@ def adjoint_ratio(steps, torch, sites=2_000_000, full_index=False):
     base = hemegb.hlb_adjoint_workspace_bytes(s._h, steps, obj.sites.size)
     extra = max(0, int(0.6 * free) - base)
     _, kept, rec, used = s.adjoint_plan(steps, obj.sites.size, base + extra)
-    if kept > 0:
+    if memory and kept > 0:
         ws = s.adjoint_workspace(steps, obj.sites.size, extra_bytes=used - base)
         s.init_equilibrium()
         torch.cuda.synchronize()
@@ -710,6 +710,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     ap.add_argument("--adjoint-sites", type=int, default=2_000_000)
     ap.add_argument("--adjoint-only", action="store_true", help="only the adjoint/forward timing")
+    ap.add_argument("--no-adjoint-memory", action="store_true",
+                    help="skip the adjoint run that keeps whole segments in most of the free device memory")
     ap.add_argument("--split-kernels", action="store_true",
                     help="the paper's per-site-type kernels on streams against the fused kernel (FP32 pull A-B)")
     ap.add_argument("--precision-study", action="store_true",
@@ -750,7 +752,8 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"adjoint": adjoint_ratio(args.adjoint_steps, torch, args.adjoint_sites,
-                                                   full_index=args.full_index)}))
+                                                   full_index=args.full_index,
+                                                   memory=not args.no_adjoint_memory)}))
     else:
         run_ours(args)
 

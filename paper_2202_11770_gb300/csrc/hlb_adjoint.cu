@@ -185,6 +185,8 @@ __device__ __forceinline__ typename Real<S>::type adjoint_site(const S* __restri
   if ((__ldg(imask + (xi >> 5)) >> (xi & 31)) & 1u) return R(0);  // iolet sites: adjoint_iolet_site
   uint32_t off[Q], fluid;
   reverse_offsets<CT, WIDE>(src, ctab, tbase, sn, n, xi, tile, off, &fluid);
+  pdl_wait();  // the states below were written by the kernels before this one
+  pdl_trigger();
   R drho, rho, ux, uy, uz, usq15;
   {
     R h[Q];
@@ -330,6 +332,8 @@ __device__ __forceinline__ typename Real<S>::type adjoint_iolet_site(const S* __
   if (w < nsites) {  // uniform across the warp
     const int64_t n = p.n, x = sites[w];
     const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
+    pdl_wait();  // the states below were written by the kernels before this one
+    pdl_trigger();
     // f(t) at x: gathered from s'(t-1) with the boundary values of G_{t-1}
     R h = R(0);
     if (GPREV) {
@@ -472,7 +476,9 @@ __global__ void __launch_bounds__(BLOCK, sizeof(typename Real<S>::type) == 8 ? 2
   }
   // block sum of the dJ/dtau terms in the kernel's arithmetic type (FP64 on
   // GB300 runs at 1/64 of the FP32 rate), accumulated per block in FP64
-  // across the reverse steps
+  // across the reverse steps (threads without a site have not waited yet)
+  pdl_wait();
+  pdl_trigger();
   const R bs = block_sum_r<R>(d, sh);
   if (threadIdx.x == 0) part[b] += (double)bs;
 }
@@ -544,10 +550,11 @@ cudaError_t launch_adjoint(const hlb_solver* h, const void* prev, bool gprev, co
               : (off32 ? k_adjoint<S, G, false, false> : k_adjoint<S, G, true, false>);
   };
   auto kernel = gprev ? pick(std::true_type{}) : pick(std::false_type{});
-  kernel<<<grid, BLOCK, 0, st>>>((const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src, h->d_ctab,
-                                 h->d_tbase, h->d_imask, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
-                                 h->n_iolet_sites, gi, make_block_div(stride), dtau_part, dlink, st_);
-  return cudaGetLastError();
+  // programmatic dependent launch: the index decode overlaps the previous
+  // kernel's tail (the reverse steps and the segment recomputes alternate)
+  return launch_pdl(kernel, grid, BLOCK, st, (const S*)prev, (const S*)cur, (const S*)mu_next, (S*)mu_out, h->d_src,
+                    h->d_ctab, h->d_tbase, h->d_imask, h->d_links, h->d_amp, ap, pm, h->d_iolet_sites,
+                    h->n_iolet_sites, gi, make_block_div(stride), dtau_part, dlink, st_);
 }
 
 struct Probe {

@@ -38,24 +38,6 @@ constexpr int BLOCK = 256;
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
-// Launch of a step-sequence kernel with programmatic stream serialisation
-// (pdl_trigger / pdl_wait in hlb_common.cuh): it may be scheduled while the
-// previous kernel of the stream finishes, and waits for it in pdl_wait.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
 // L2 prefetch hint: `bytes` (a multiple of 16) from a 16-byte aligned address.
 __device__ __forceinline__ void l2_prefetch(const void* q, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(q)), "r"(bytes)

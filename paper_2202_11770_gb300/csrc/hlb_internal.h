@@ -115,6 +115,24 @@ int hlb_no_throw(F f) {
   }
 }
 
+// Launch of a step-sequence kernel with programmatic stream serialisation
+// (pdl_trigger / pdl_wait in hlb_common.cuh): it may be scheduled while the
+// previous kernel of the stream finishes, and waits for it in pdl_wait.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---- launchers (hlb_forward.cu) ----
 // One pull A-B time step from fin into fout (gather: fin holds s'(t-1)).
 cudaError_t hlb_launch_step(const hlb_solver* h, const void* fin, void* fout, bool gather, int64_t tb,
