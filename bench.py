@@ -624,7 +624,10 @@ def run_ours(args):
     kname = kernel_names(n, compact, args.wide_offsets)[0 if scheme == "ab" else 1]
     kst = head["kernels"][kname]
     traffic = None
-    if (TRAFFIC["sha"] == kernel_sha() and TRAFFIC["index"] == ("compact" if compact else "int32")
+    # the recorded bytes belong to the 32-bit-offset kernels (lattices below
+    # ~226M sites without --wide-offsets); larger lattices run the wide form
+    off32 = not args.wide_offsets and 19 * ((n + 3) // 4 * 4) <= 0xFFFFFFFF
+    if (TRAFFIC["sha"] == kernel_sha() and TRAFFIC["index"] == ("compact" if compact else "int32") and off32
             and kname in TRAFFIC["bytes_per_site"]):
         traffic = TRAFFIC["bytes_per_site"][kname] * n
 
