@@ -56,3 +56,21 @@ def test_kernel_names_follow_the_launch_rule():
     assert bench.kernel_names(20_000_865)[0] == "k_step"
     assert bench.kernel_names(20_000_864, compact=False)[0] == "k_step"
     assert bench.kernel_names(20_000_864, wide=True)[0] == "k_step"
+
+
+def test_reference_arm_runs_the_requested_steps(tmp_path):
+    """The oracle arm runs exactly --warmup and --steps, here on a smaller tree
+    of the same generator because the full-lattice steps exceed the budget;
+    the line keeps the full workload's config."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, str(bench.ROOT / "bench.py"), "--impl", "reference", "--sites", "2000000",
+                        "--steps", "2", "--warmup", "1", "--ref-budget", "0.01"],
+                       capture_output=True, text=True, timeout=600, cwd=tmp_path)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["config"]["n_sites"] > 1_900_000 and line["value"] > 0
+    assert "smaller tree" in line["cpu_baseline"]["sample"] and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["value"] == line["value"]
