@@ -45,7 +45,7 @@ __device__ __forceinline__ void l2_prefetch(const void* q, uint32_t bytes) {
 }
 
 // Called by the first warp of a bulk block: prefetch into L2 what the block
-// that takes tile `tile` (about one wave of resident blocks later) reads
+// that takes tile `tile` (about a wave of resident blocks later) reads
 // first, so that its loads find L2 instead of waiting on DRAM.  Lanes 0-8:
 // the tile's compact index words (row q, 256 sites).  With POPS, lanes
 // 9-26: for direction i = lane - 8, the population row its gathers read
@@ -499,9 +499,11 @@ __global__ void __launch_bounds__(256) k_aa_fix(S* A, const int32_t* __restrict_
 // offsets within direction pairs (lattices above ~226M sites), which need a
 // few more registers: four blocks per SM (64 registers) measured 8 % faster
 // than five with their spills.  CT: codes from the compact index table, and
-// the first warp prefetches into L2 the tile `pf` blocks ahead (one wave of
-// resident blocks; 0: none): index words, and for 4- and 8-byte storage the
-// gathered rows (for 16-bit storage the rows measured slower).
+// the first warp prefetches into L2 the tile `pf` blocks ahead (0: none):
+// index words, and for 4- and 8-byte storage the gathered rows (for 16-bit
+// storage the rows measured slower).  With 32-bit offsets pf is 3 blocks per
+// SM, 0.6 of a wave: FP32 odd step 608 us at one wave, 599 us at 0.6, 615 us
+// at 0.2 (16-bit unchanged); the wide form keeps one wave (4 blocks per SM).
 template <typename S, bool WIDE, bool CT>
 __global__ void __launch_bounds__(BLOCK, WIDE ? 4 : 5) k_aa_odd(S* A, const int32_t* __restrict__ src,
                                                                const uint32_t* __restrict__ ctab,
@@ -880,7 +882,7 @@ struct AAOp {
       e = launch_pdl(h->compact ? (h->off32 ? k_aa_odd<S, false, true> : k_aa_odd<S, true, true>)
                                 : (h->off32 ? k_aa_odd<S, false, false> : k_aa_odd<S, true, false>),
                      grid_for(h->n), BLOCK, s, (S*)A, h->d_src, h->d_ctab, h->d_tbase,
-                     (uint32_t)h->n_sm * (h->off32 ? 5u : 4u), p);
+                     (uint32_t)h->n_sm * (h->off32 ? 3u : 4u), p);
     else
       e = aa_even<S>(h, (S*)A, p, s);
     if (e != cudaSuccess || h->n_iolet_sites == 0) return e;
