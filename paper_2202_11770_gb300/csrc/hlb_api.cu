@@ -278,6 +278,38 @@ extern "C" int hlb_workspace_bytes(const hlb_lattice* L, const hlb_options* o, s
   return hlb_no_throw([&] { return workspace_bytes_impl(L, o, bytes); });
 }
 
+namespace {
+
+// Iolet links re-coded to their records at create: record r (site x,
+// direction j) gets the code -(2 + r) in row j - 1.
+__global__ void k_recode(int32_t* __restrict__ src, int64_t sn, const LinkRec* __restrict__ links, int64_t nlinks) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nlinks) return;
+  const LinkRec L = links[r];
+  src[(int64_t)(L.dir - 1) * sn + L.site] = -(int32_t)(2 + r);
+}
+
+// The 18 codes of each iolet site, contiguous: icode[q][i - 1].
+__global__ void k_icode(const int32_t* __restrict__ src, int64_t sn, const int32_t* __restrict__ sites, int64_t nsites,
+                        int32_t* __restrict__ icode) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nsites * (Q - 1)) return;
+  const int64_t q = k / (Q - 1);
+  const int i = (int)(k - q * (Q - 1));
+  icode[k] = src[(int64_t)i * sn + sites[q]];
+}
+
+}  // namespace
+
+cudaError_t hlb_launch_recode(const hlb_solver* h, cudaStream_t s) {
+  k_recode<<<(unsigned)((h->n_links + 255) / 256), 256, 0, s>>>(h->d_src, h->sn, h->d_links, h->n_links);
+  return cudaGetLastError();
+}
+cudaError_t hlb_launch_icode(const hlb_solver* h, cudaStream_t s) {
+  const int64_t k = h->n_iolet_sites * (Q - 1);
+  k_icode<<<(unsigned)((k + 255) / 256), 256, 0, s>>>(h->d_src, h->sn, h->d_iolet_sites, h->n_iolet_sites, h->d_icode);
+  return cudaGetLastError();
+}
 static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, size_t ws_bytes, hlb_stream stream,
                        hlb_solver** out, std::unique_ptr<hlb_solver>* owner) {
   if (!out) return hlb_fail(HLB_ERR_ARG, "null output");
@@ -397,18 +429,6 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   }
   std::vector<LinkRec> recs((size_t)std::max<int64_t>(y.n_links, 1));
   const int64_t sn = h->sn;
-  std::vector<int32_t> src((size_t)18 * sn);
-  {
-    // the caller's rows into the padded table, one thread per row; padding
-    // entries (never gathered) are -1
-    std::vector<std::thread> pool;
-    for (int i = 0; i < 18; ++i)
-      pool.emplace_back([&, i] {
-        std::copy(L->src + (size_t)i * n, L->src + (size_t)(i + 1) * n, src.begin() + (size_t)i * sn);
-        std::fill(src.begin() + (size_t)i * sn + n, src.begin() + (size_t)(i + 1) * sn, -1);
-      });
-    for (auto& t : pool) t.join();
-  }
   for (int64_t r = 0; r < (int64_t)links.size(); ++r) {
     const int64_t x = links[(size_t)r].x;
     const int j = links[(size_t)r].dir;
@@ -439,7 +459,6 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
         R.coef = 6.0 * wgt<double>(j) * W * cn;
       }
       R.coef_f = (float)R.coef;
-      src[(size_t)(j - 1) * sn + x] = -(int32_t)(2 + r);
     }
   }
 
@@ -453,15 +472,23 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   std::sort(isites.begin(), isites.end());
   isites.erase(std::unique(isites.begin(), isites.end()), isites.end());
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_src, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, st);
+  // the caller's rows straight into the padded device table (no host copy of
+  // the table), padding entries (never gathered) -1, then the iolet links
+  // re-coded to their records on the device
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(h->d_src, sizeof(int32_t) * (size_t)sn, L->src, sizeof(int32_t) * (size_t)n,
+                          sizeof(int32_t) * (size_t)n, 18, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && sn > n)
+    e = cudaMemset2DAsync(h->d_src + n, sizeof(int32_t) * (size_t)sn, 0xff, sizeof(int32_t) * (size_t)(sn - n), 18, st);
+  if (e == cudaSuccess && y.n_links > 0)
+    e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && y.n_links > 0) e = hlb_launch_recode(h, st);
   // compact index table from the re-coded one; the fit flag comes back with
   // the final synchronisation
   int32_t misfit = 1;
   if (e == cudaSuccess) e = cudaMemsetAsync(d_misfit, 0, sizeof(int32_t), st);
   if (e == cudaSuccess) e = hlb_launch_ctab(h, d_misfit, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&misfit, d_misfit, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess && y.n_links > 0)
-    e = cudaMemcpyAsync(h->d_links, recs.data(), sizeof(LinkRec) * (size_t)y.n_links, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_amp, ampf.data(), sizeof(double) * ampf.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_ampf, 0, sizeof(float) * ampf.size(), st);
   if (e == cudaSuccess && h->d_normal)
@@ -471,11 +498,7 @@ static int create_impl(const hlb_lattice* L, const hlb_options* o, void* ws, siz
   if (e == cudaSuccess && nis > 0)
     e = cudaMemcpyAsync(h->d_iolet_sites, isites.data(), sizeof(int32_t) * (size_t)nis, cudaMemcpyHostToDevice, st);
   // index codes of the iolet sites (the library's own re-coded table), 18 per site
-  std::vector<int32_t> icode((size_t)18 * (size_t)nis);
-  for (int64_t q = 0; q < nis; ++q)
-    for (int i = 1; i < Q; ++i) icode[(size_t)q * 18 + (i - 1)] = src[(size_t)(i - 1) * sn + isites[q]];
-  if (e == cudaSuccess && nis > 0)
-    e = cudaMemcpyAsync(h->d_icode, icode.data(), sizeof(int32_t) * icode.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nis > 0) e = hlb_launch_icode(h, st);
   // bit mask of the sites with an iolet link (bulk threads of k_step leave them to the iolet warps)
   std::vector<uint32_t> imask((size_t)((n + 31) / 32), 0u);
   for (int32_t x : isites) imask[(size_t)x >> 5] |= 1u << (x & 31);

@@ -161,6 +161,12 @@ cudaError_t hlb_launch_monitor(const hlb_solver* h, const void* fin, int mode, i
 // Shifted pre-collision state into out [19][n] (row < 0) or direction `row` into out [n].
 cudaError_t hlb_launch_state(const hlb_solver* h, const void* fin, int mode, int64_t tb, void* out, int row,
                              cudaStream_t s);
+// Iolet links of d_src re-coded to -(2 + record) from the uploaded link
+// records (d_links: site, direction).
+cudaError_t hlb_launch_recode(const hlb_solver* h, cudaStream_t s);
+// d_icode[q][i - 1] = d_src[i - 1][d_iolet_sites[q]]: the 18 codes of every
+// iolet site, contiguous (after hlb_launch_recode).
+cudaError_t hlb_launch_icode(const hlb_solver* h, cudaStream_t s);
 // Compact index table from d_src; *misfit (device, zeroed by the caller)
 // becomes nonzero if some tile's sources span more than a 16-bit offset.
 cudaError_t hlb_launch_ctab(const hlb_solver* h, int32_t* misfit, cudaStream_t s);
