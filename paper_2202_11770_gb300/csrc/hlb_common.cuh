@@ -373,10 +373,11 @@ __device__ __forceinline__ void iolet_fixup(const S* __restrict__ fin, const int
 }
 
 // ---------------------------------------------------------------------------
-// Warp-cooperative boundary sites: one warp per site, lane i = direction i
-// (lanes 19..31 idle).  Moments are summed by a shuffle loop in direction
-// order with exactly the operations of the per-thread code above, so a site
-// gets bit-identical values whichever path processes it.
+// Warp-cooperative boundary sites: a lane per direction (the adjoint: one
+// warp a site, lanes 19..31 idle; the forward kernels: a half-warp a site,
+// three lanes holding two directions).  Moments are summed by a shuffle loop
+// in direction order with exactly the operations of the per-thread code
+// above, so a site gets bit-identical values whichever path processes it.
 // ---------------------------------------------------------------------------
 constexpr unsigned FULL_MASK = 0xffffffffu;
 static __constant__ int8_t k_cx[32] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -401,14 +402,6 @@ __device__ __forceinline__ R lane_heq(int i, R drho, R rho, R ux, R uy, R uz, R 
   R cu = lane_cdotu<R>(i, ux, uy, uz);
   return lane_w<R>(i) * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - usq15));
 }
-// sum over lanes 0..18 of v (direction order), every lane gets the result
-template <typename R>
-__device__ __forceinline__ R lane_sum(R v) {
-  R acc = R(0);
-#pragma unroll
-  for (int k = 0; k < Q; ++k) acc += __shfl_sync(FULL_MASK, v, k);
-  return acc;
-}
 // (sum v, sum v c) over lanes 0..18 in direction order; sgn = -1 sums -v c
 template <typename R>
 __device__ __forceinline__ void lane_moment_sums(R v, R sgn, R* d, R* jx, R* jy, R* jz) {
@@ -423,52 +416,6 @@ __device__ __forceinline__ void lane_moment_sums(R v, R sgn, R* d, R* jx, R* jy,
   }
   *d = a; *jx = x; *jy = y; *jz = z;
 }
-// moments() of a distributed vector (u = j * (1/rho), as moments() does)
-template <typename R>
-__device__ __forceinline__ Macro<R> lane_moments(R v) {
-  Macro<R> m;
-  R jx, jy, jz;
-  lane_moment_sums<R>(v, R(1), &m.drho, &jx, &jy, &jz);
-  m.rho = R(1) + m.drho;
-  const R inv = R(1) / m.rho;
-  m.ux = jx * inv;
-  m.uy = jy * inv;
-  m.uz = jz * inv;
-  return m;
-}
-// collide() of a site held one direction per lane (lane i = direction i,
-// lanes 19..31 return 0), with the operations of collide_emit() in the same
-// order, so that a site gets the same bits whichever path steps it.
-template <typename R>
-__device__ __forceinline__ R lane_collide(R h, int i, R omega) {
-  R drho = __shfl_sync(FULL_MASK, h, 0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-  for (int p = 0; p < 9; ++p) {
-    const int ip = 2 * p + 1;
-    const R a = __shfl_sync(FULL_MASK, h, ip), b = __shfl_sync(FULL_MASK, h, ip + 1);
-    const R sp = a + b, dp = a - b;
-    drho += sp;
-    if (cx(ip)) jx = cx(ip) > 0 ? jx + dp : jx - dp;
-    if (cy(ip)) jy = cy(ip) > 0 ? jy + dp : jy - dp;
-    if (cz(ip)) jz = cz(ip) > 0 ? jz + dp : jz - dp;
-  }
-  const R rho = R(1) + drho;
-  const R inv = R(1) / rho;
-  const R ux = jx * inv, uy = jy * inv, uz = jz * inv;
-  const R usq15 = R(1.5) * fmadd(uz, uz, fmadd(uy, uy, ux * ux));
-  const R om1 = R(1) - omega;
-  if (i >= Q) return R(0);
-  if (i == 0) {
-    const R ow = omega * wgt<R>(0);
-    return fmadd(om1, h, fmadd(-(ow * rho), usq15, ow * drho));
-  }
-  const int ip = 2 * ((i - 1) >> 1) + 1;
-  const R ow = omega * (ip <= 6 ? wgt<R>(1) : wgt<R>(7));
-  const R cu = lane_cdotu<R>(ip, ux, uy, uz);
-  const R a = fmadd(R(4.5) * cu, cu, -usq15);
-  return fmadd(om1, h, fmadd(ow * rho, fmadd((i & 1) ? R(3) : R(-3), cu, a), ow * drho));
-}
-
 // Boundary value of the lane's iolet link (as iolet_fixup computes it):
 // `out` = s'_ibar(x); rho_s, u_s the moments of the stored post-collision state.
 template <typename R>

@@ -96,43 +96,96 @@ __global__ void __launch_bounds__(BLOCK) k_step_local(const S* __restrict__ fin,
   collide_emit<R>(h, omega_of<R>(p), [&](int i, R v) { stpop<S>(fout + (int64_t)i * n + x, v); });
 }
 
-// The same step for the sites with iolet links: one warp per site, lane i
-// handles direction i (gather, boundary value, collision), with the moment
-// sums in direction order so that every value equals the per-thread
-// read-back path (iolet_fixup) bit for bit.
+// The same step for the sites with iolet links, two sites a warp: 16 lanes a
+// site, lane h holding direction h and, for h < 3, also direction 16 + h
+// (gather, boundary value, collision).  Moments and collision sums run over
+// the directions in the order of the per-thread code (collide_emit, and the
+// read-back path iolet_fixup), so every value equals it bit for bit.  w is
+// the half-warp's site; a half-warp past the end shadows site 0 and stores
+// nothing (all 32 lanes take part in the shuffles).
+template <typename R>
+__device__ __forceinline__ R half_get(R v0, R v1, int k) {
+  return __shfl_sync(FULL_MASK, k < 16 ? v0 : v1, k & 15, 16);
+}
+// Post-collision population of direction i from the site's sums, with the
+// operations of collide_emit.
+template <typename R>
+__device__ __forceinline__ R half_out(int i, R h, R omega, R drho, R rho, R ux, R uy, R uz, R usq15) {
+  const R om1 = R(1) - omega;
+  if (i == 0) {
+    const R ow = omega * wgt<R>(0);
+    return fmadd(om1, h, fmadd(-(ow * rho), usq15, ow * drho));
+  }
+  const int ip = 2 * ((i - 1) >> 1) + 1;
+  const R ow = omega * (ip <= 6 ? wgt<R>(1) : wgt<R>(7));
+  const R cu = lane_cdotu<R>(ip, ux, uy, uz);
+  const R a = fmadd(R(4.5) * cu, cu, -usq15);
+  return fmadd(om1, h, fmadd(ow * rho, fmadd((i & 1) ? R(3) : R(-3), cu, a), ow * drho));
+}
 template <typename S>
 __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __restrict__ fout,
                                                 const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
                                                 int64_t nsites, const StepParams& p, int64_t w) {
   using R = typename Real<S>::type;
-  if (w >= nsites) return;  // uniform across the warp
-  const int i = threadIdx.x & 31;
-  const bool dir = i < Q;
-  const int64_t n = p.n, x = sites[w];
-  const int32_t code = (dir && i > 0) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
-  // the link record and amplitude load beside the populations, not after
-  // them (record 0 exists whenever a site has an iolet link)
-  const LinkRec L = links[code <= -2 ? -code - 2 : 0];
-  R h = R(0), own = R(0);
-  if (dir) {
-    h = ldpop(fin + (i == 0 ? x : (code >= 0 ? (int64_t)i * n + code : (int64_t)lane_opp(i) * n + x)));
-    own = ldpop(fin + (int64_t)i * n + x);
+  const bool live = w < nsites;
+  const int i0 = threadIdx.x & 15, i1 = 16 + i0;
+  const bool two = i0 < Q - 16;
+  const int64_t n = p.n, x = sites[live ? w : 0];
+  const int32_t c0 = i0 > 0 ? src[(int64_t)(i0 - 1) * p.sn + x] : 0;
+  const int32_t c1 = two ? src[(int64_t)(i1 - 1) * p.sn + x] : 0;
+  // link records and amplitudes load beside the populations, not after them
+  // (record 0 exists whenever a site has an iolet link)
+  const LinkRec L0 = links[c0 <= -2 ? -c0 - 2 : 0], L1 = links[c1 <= -2 ? -c1 - 2 : 0];
+  R h0 = ldpop(fin + (i0 == 0 ? x : (c0 >= 0 ? (int64_t)i0 * n + c0 : (int64_t)lane_opp(i0) * n + x)));
+  const R own0 = ldpop(fin + (int64_t)i0 * n + x);
+  R h1 = R(0), own1 = R(0);
+  if (two) {
+    h1 = ldpop(fin + (c1 >= 0 ? (int64_t)i1 * n + c1 : (int64_t)lane_opp(i1) * n + x));
+    own1 = ldpop(fin + (int64_t)i1 * n + x);
   }
-  const R a = BC<R>::amp(p, amp, L.kind == 0 && L.group >= 0 ? L.group : 0);
-  R d, jx, jy, jz;
-  lane_moment_sums<R>(own, R(1), &d, &jx, &jy, &jz);
+  const R a0 = BC<R>::amp(p, amp, L0.kind == 0 && L0.group >= 0 ? L0.group : 0);
+  const R a1 = BC<R>::amp(p, amp, L1.kind == 0 && L1.group >= 0 ? L1.group : 0);
+  // moments of the stored s'(t-1) at x, in direction order
+  R d = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    const R vk = half_get(own0, own1, k);
+    d += vk;
+    if (cx(k)) jx += cx(k) > 0 ? vk : -vk;
+    if (cy(k)) jy += cy(k) > 0 ? vk : -vk;
+    if (cz(k)) jz += cz(k) > 0 ? vk : -vk;
+  }
   const R rho_s = R(1) + d;
   const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
-  if (code <= -2) h = lane_iolet_value<R>(i, L, h, rho_s, ux, uy, uz, a, p);
-  h = lane_collide<R>(h, i, omega_of<R>(p));
-  if (dir) stpop<S>(fout + (int64_t)i * n + x, h);
+  if (c0 <= -2) h0 = lane_iolet_value<R>(i0, L0, h0, rho_s, ux, uy, uz, a0, p);
+  if (c1 <= -2) h1 = lane_iolet_value<R>(i1, L1, h1, rho_s, ux, uy, uz, a1, p);
+  // collision: sums over opposite pairs as collide_emit forms them
+  const R omega = omega_of<R>(p);
+  R drho = half_get(h0, h1, 0), cjx = R(0), cjy = R(0), cjz = R(0);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const int ip = 2 * q + 1;
+    const R va = half_get(h0, h1, ip), vb = half_get(h0, h1, ip + 1);
+    const R sp = va + vb, dp = va - vb;
+    drho += sp;
+    if (cx(ip)) cjx = cx(ip) > 0 ? cjx + dp : cjx - dp;
+    if (cy(ip)) cjy = cy(ip) > 0 ? cjy + dp : cjy - dp;
+    if (cz(ip)) cjz = cz(ip) > 0 ? cjz + dp : cjz - dp;
+  }
+  const R rho = R(1) + drho;
+  const R inv = R(1) / rho;
+  const R cux = cjx * inv, cuy = cjy * inv, cuz = cjz * inv;
+  const R usq15 = R(1.5) * fmadd(cuz, cuz, fmadd(cuy, cuy, cux * cux));
+  if (!live) return;
+  stpop<S>(fout + (int64_t)i0 * n + x, half_out<R>(i0, h0, omega, drho, rho, cux, cuy, cuz, usq15));
+  if (two) stpop<S>(fout + (int64_t)i1 * n + x, half_out<R>(i1, h1, omega, drho, rho, cux, cuy, cuz, usq15));
 }
 
 // Pull A-B step from s'(t-1) in one launch: gather f(t) through the index
 // table (walls: the site's own opposite slot), collide, store coalesced.
-// Every stride-th block (the first n_iolet_blocks of them) takes eight
-// iolet sites, a warp each (step_iolet_site); the others take 256 bulk sites,
+// Every stride-th block (the first n_iolet_blocks of them) takes sixteen
+// iolet sites, a half-warp each (step_iolet_site); the others take 256 bulk sites,
 // a thread each, and leave iolet sites alone.  The iolet blocks, spread
 // through the grid, run beside the bulk blocks instead of after them.
 // WIDE: offsets within direction pairs (lattices above ~226M sites).  CT:
@@ -151,7 +204,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
   if (b == j * stride.d && j < n_iolet_blocks) {
     pdl_wait();
     pdl_trigger();
-    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
+    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 4);
     return;
   }
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
@@ -368,7 +421,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_step2(const S* __restrict__ fin, S
   if (b == j * stride.d && j < n_iolet_blocks) {
     pdl_wait();
     pdl_trigger();
-    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 5);
+    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 4);
     return;
   }
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
@@ -842,7 +895,7 @@ cudaError_t dispatch(int precision, A... a) {
 template <typename S>
 cudaError_t launch_gather(const hlb_solver* h, const void* fin, void* fout, const StepParams& p, uint32_t tile0,
                           uint32_t ntiles, bool iolets, cudaStream_t s) {
-  const unsigned gi = iolets ? (unsigned)((h->n_iolet_sites + 7) / 8) : 0u;  // 8 warps (sites) per block
+  const unsigned gi = iolets ? (unsigned)((h->n_iolet_sites + 15) / 16) : 0u;  // 16 half-warps (sites) per block
   const unsigned grid = gi + ntiles;
   if (grid == 0) return cudaSuccess;
   if constexpr (sizeof(S) <= 4) {
