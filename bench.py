@@ -81,12 +81,12 @@ CTYPE = {"fp32": "float", "bf16": "__nv_bfloat16", "fp16": "__half", "fp64": "do
 # DRAM traffic per site update from one ncu capture (profiles/), valid only
 # while the kernel sources hash to the recorded value.
 TRAFFIC_FILES = ["paper_2202_11770_gb300/csrc/hlb_common.cuh", "paper_2202_11770_gb300/csrc/hlb_forward.cu"]
-TRAFFIC = {"sha": "61b4bd4ba06394e9",
+TRAFFIC = {"sha": "67b390820d1752e1",
            # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (mean of two), 20,000,864-site
            # tree, kernels on the compact index table with the L2 prefetch
            "index": "compact",
-           "bytes_per_site": {"k_aa_odd": ((2265914112 + 1483236096) + (2266237952 + 1480719872)) / 2 / 20000864,
-                              "k_step2": ((2371848448 + 1485402880) + (2366041344 + 1480676096)) / 2 / 20000864}}
+           "bytes_per_site": {"k_aa_odd": ((2265953280 + 1483422208) + (2266168576 + 1480823808)) / 2 / 20000864,
+                              "k_step2": ((2373115392 + 1484953600) + (2366690304 + 1480613632)) / 2 / 20000864}}
 
 
 def kernel_sha() -> str:

@@ -35,6 +35,12 @@ using namespace hlb;
 namespace {
 
 constexpr int BLOCK = 256;
+// Lanes a site for the iolet sites: a site's 19 directions spread over them,
+// up to ceil(19 / lanes) a lane.  Measured on the 20M-site tree: the pull
+// step's iolet sites 8 lanes (BF16 step 411 -> 405 us against 16, 418 at 32),
+// the AA iolet pass 16 (8 lanes 1-2 us slower a step, 32 lanes 3 us slower).
+constexpr int kStepIoletLanes = 8;
+constexpr int kFixLanes = 16;
 
 inline unsigned grid_for(int64_t n) { return (unsigned)((n + BLOCK - 1) / BLOCK); }
 
@@ -96,21 +102,10 @@ __global__ void __launch_bounds__(BLOCK) k_step_local(const S* __restrict__ fin,
   collide_emit<R>(h, omega_of<R>(p), [&](int i, R v) { stpop<S>(fout + (int64_t)i * n + x, v); });
 }
 
-// The same step for the sites with iolet links, two sites a warp: 16 lanes a
-// site, lane h holding direction h and, for h < 3, also direction 16 + h
-// (gather, boundary value, collision).  Moments and collision sums run over
-// the directions in the order of the per-thread code (collide_emit, and the
-// read-back path iolet_fixup), so every value equals it bit for bit.  w is
-// the half-warp's site; a half-warp past the end shadows site 0 and stores
-// nothing (all 32 lanes take part in the shuffles).
-template <typename R>
-__device__ __forceinline__ R half_get(R v0, R v1, int k) {
-  return __shfl_sync(FULL_MASK, k < 16 ? v0 : v1, k & 15, 16);
-}
 // Post-collision population of direction i from the site's sums, with the
 // operations of collide_emit.
 template <typename R>
-__device__ __forceinline__ R half_out(int i, R h, R omega, R drho, R rho, R ux, R uy, R uz, R usq15) {
+__device__ __forceinline__ R iolet_lane_out(int i, R h, R omega, R drho, R rho, R ux, R uy, R uz, R usq15) {
   const R om1 = R(1) - omega;
   if (i == 0) {
     const R ow = omega * wgt<R>(0);
@@ -122,35 +117,45 @@ __device__ __forceinline__ R half_out(int i, R h, R omega, R drho, R rho, R ux, 
   const R a = fmadd(R(4.5) * cu, cu, -usq15);
   return fmadd(om1, h, fmadd(ow * rho, fmadd((i & 1) ? R(3) : R(-3), cu, a), ow * drho));
 }
+// The same step for the sites with iolet links, kStepIoletLanes lanes a
+// site, lane h holding directions h, h + lanes, ... (gather, boundary value,
+// collision).  Moments and collision sums run over the directions in the
+// order of the per-thread code (collide_emit, and the read-back path
+// iolet_fixup), so every value equals it bit for bit.  w is the lane
+// group's site; a group past the end shadows site 0 and stores nothing (all
+// 32 lanes take part in the shuffles).
 template <typename S>
 __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __restrict__ fout,
                                                 const int32_t* __restrict__ src, const LinkRec* __restrict__ links,
                                                 const double* __restrict__ amp, const int32_t* __restrict__ sites,
                                                 int64_t nsites, const StepParams& p, int64_t w) {
   using R = typename Real<S>::type;
+  constexpr int W = kStepIoletLanes, NE = (Q + W - 1) / W;
   const bool live = w < nsites;
-  const int i0 = threadIdx.x & 15, i1 = 16 + i0;
-  const bool two = i0 < Q - 16;
+  const int hl = threadIdx.x & (W - 1);
   const int64_t n = p.n, x = sites[live ? w : 0];
-  const int32_t c0 = i0 > 0 ? src[(int64_t)(i0 - 1) * p.sn + x] : 0;
-  const int32_t c1 = two ? src[(int64_t)(i1 - 1) * p.sn + x] : 0;
-  // link records and amplitudes load beside the populations, not after them
-  // (record 0 exists whenever a site has an iolet link)
-  const LinkRec L0 = links[c0 <= -2 ? -c0 - 2 : 0], L1 = links[c1 <= -2 ? -c1 - 2 : 0];
-  R h0 = ldpop(fin + (i0 == 0 ? x : (c0 >= 0 ? (int64_t)i0 * n + c0 : (int64_t)lane_opp(i0) * n + x)));
-  const R own0 = ldpop(fin + (int64_t)i0 * n + x);
-  R h1 = R(0), own1 = R(0);
-  if (two) {
-    h1 = ldpop(fin + (c1 >= 0 ? (int64_t)i1 * n + c1 : (int64_t)lane_opp(i1) * n + x));
-    own1 = ldpop(fin + (int64_t)i1 * n + x);
+  int32_t c[NE];
+  LinkRec L[NE];
+  R h[NE], own[NE], a[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int i = e * W + hl;
+    c[e] = (i >= 1 && i < Q) ? src[(int64_t)(i - 1) * p.sn + x] : 0;
+    // link records and amplitudes load beside the populations, not after
+    // them (record 0 exists whenever a site has an iolet link)
+    L[e] = links[c[e] <= -2 ? -c[e] - 2 : 0];
+    h[e] = own[e] = R(0);
+    if (i < Q) {
+      h[e] = ldpop(fin + (i == 0 ? x : (c[e] >= 0 ? (int64_t)i * n + c[e] : (int64_t)lane_opp(i) * n + x)));
+      own[e] = ldpop(fin + (int64_t)i * n + x);
+    }
+    a[e] = BC<R>::amp(p, amp, L[e].kind == 0 && L[e].group >= 0 ? L[e].group : 0);
   }
-  const R a0 = BC<R>::amp(p, amp, L0.kind == 0 && L0.group >= 0 ? L0.group : 0);
-  const R a1 = BC<R>::amp(p, amp, L1.kind == 0 && L1.group >= 0 ? L1.group : 0);
   // moments of the stored s'(t-1) at x, in direction order
   R d = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    const R vk = half_get(own0, own1, k);
+    const R vk = __shfl_sync(FULL_MASK, own[k / W], k % W, W);
     d += vk;
     if (cx(k)) jx += cx(k) > 0 ? vk : -vk;
     if (cy(k)) jy += cy(k) > 0 ? vk : -vk;
@@ -158,15 +163,16 @@ __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __
   }
   const R rho_s = R(1) + d;
   const R ux = jx / rho_s, uy = jy / rho_s, uz = jz / rho_s;
-  if (c0 <= -2) h0 = lane_iolet_value<R>(i0, L0, h0, rho_s, ux, uy, uz, a0, p);
-  if (c1 <= -2) h1 = lane_iolet_value<R>(i1, L1, h1, rho_s, ux, uy, uz, a1, p);
+#pragma unroll
+  for (int e = 0; e < NE; ++e)
+    if (c[e] <= -2) h[e] = lane_iolet_value<R>(e * W + hl, L[e], h[e], rho_s, ux, uy, uz, a[e], p);
   // collision: sums over opposite pairs as collide_emit forms them
   const R omega = omega_of<R>(p);
-  R drho = half_get(h0, h1, 0), cjx = R(0), cjy = R(0), cjz = R(0);
+  R drho = __shfl_sync(FULL_MASK, h[0], 0, W), cjx = R(0), cjy = R(0), cjz = R(0);
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
     const int ip = 2 * q + 1;
-    const R va = half_get(h0, h1, ip), vb = half_get(h0, h1, ip + 1);
+    const R va = __shfl_sync(FULL_MASK, h[ip / W], ip % W, W), vb = __shfl_sync(FULL_MASK, h[(ip + 1) / W], (ip + 1) % W, W);
     const R sp = va + vb, dp = va - vb;
     drho += sp;
     if (cx(ip)) cjx = cx(ip) > 0 ? cjx + dp : cjx - dp;
@@ -178,14 +184,17 @@ __device__ __forceinline__ void step_iolet_site(const S* __restrict__ fin, S* __
   const R cux = cjx * inv, cuy = cjy * inv, cuz = cjz * inv;
   const R usq15 = R(1.5) * fmadd(cuz, cuz, fmadd(cuy, cuy, cux * cux));
   if (!live) return;
-  stpop<S>(fout + (int64_t)i0 * n + x, half_out<R>(i0, h0, omega, drho, rho, cux, cuy, cuz, usq15));
-  if (two) stpop<S>(fout + (int64_t)i1 * n + x, half_out<R>(i1, h1, omega, drho, rho, cux, cuy, cuz, usq15));
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int i = e * W + hl;
+    if (i < Q) stpop<S>(fout + (int64_t)i * n + x, iolet_lane_out<R>(i, h[e], omega, drho, rho, cux, cuy, cuz, usq15));
+  }
 }
 
 // Pull A-B step from s'(t-1) in one launch: gather f(t) through the index
 // table (walls: the site's own opposite slot), collide, store coalesced.
-// Every stride-th block (the first n_iolet_blocks of them) takes sixteen
-// iolet sites, a half-warp each (step_iolet_site); the others take 256 bulk sites,
+// Every stride-th block (the first n_iolet_blocks of them) takes 32 iolet
+// sites, 8 lanes each (step_iolet_site); the others take 256 bulk sites,
 // a thread each, and leave iolet sites alone.  The iolet blocks, spread
 // through the grid, run beside the bulk blocks instead of after them.
 // WIDE: offsets within direction pairs (lattices above ~226M sites).  CT:
@@ -204,7 +213,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_step(const S* __restrict__ fin, S*
   if (b == j * stride.d && j < n_iolet_blocks) {
     pdl_wait();
     pdl_trigger();
-    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 4);
+    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) / kStepIoletLanes);
     return;
   }
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(BLOCK, 3) k_step2(const S* __restrict__ fin, S
   if (b == j * stride.d && j < n_iolet_blocks) {
     pdl_wait();
     pdl_trigger();
-    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) >> 4);
+    step_iolet_site<S>(fin, fout, src, links, amp, sites, nsites, p, ((int64_t)j * BLOCK + threadIdx.x) / kStepIoletLanes);
     return;
   }
   const uint32_t n = (uint32_t)p.n, sn = (uint32_t)p.sn;
@@ -518,34 +527,40 @@ __global__ void __launch_bounds__(256, 8) k_aa_fix(S* A, const int32_t* __restri
                                                  const int32_t* __restrict__ sites, int64_t nsites,
                                                  const StepParams p, double* __restrict__ lflux) {
   using R = typename Real<S>::type;
-  const int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  constexpr int W = kFixLanes, NE = (Q + W - 1) / W;
+  const int64_t q0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const bool live = q0 < nsites;
-  const int64_t q = live ? q0 : 0;  // a half-warp past the end shadows site 0 and stores nothing
-  const int i0 = threadIdx.x & 15, i1 = 16 + i0;
-  const bool two = i0 < Q - 16;
+  const int64_t q = live ? q0 : 0;  // lanes past the end shadow site 0 and store nothing
+  const int hl = threadIdx.x & (W - 1);
   const int64_t x = __ldg(sites + q);
-  const int32_t c0 = i0 >= 1 ? __ldg(icode + q * (Q - 1) + (i0 - 1)) : 0;
-  const int32_t c1 = two ? __ldg(icode + q * (Q - 1) + (i1 - 1)) : 0;
-  // link records and amplitudes do not change between steps: loaded before
-  // the wait for the step kernel (record 0 exists whenever there are iolet sites)
-  const LinkRec L0 = links[c0 <= -2 ? -c0 - 2 : 0], L1 = links[c1 <= -2 ? -c1 - 2 : 0];
-  const R a0 = BC<R>::amp(p, amp, L0.kind == 0 && L0.group >= 0 ? L0.group : 0);
-  const R a1 = BC<R>::amp(p, amp, L1.kind == 0 && L1.group >= 0 ? L1.group : 0);
+  int32_t c[NE];
+  LinkRec L[NE];
+  R a[NE], v[NE];
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int i = e * W + hl;
+    c[e] = (i >= 1 && i < Q) ? __ldg(icode + q * (Q - 1) + (i - 1)) : 0;
+    // link records and amplitudes do not change between steps: loaded before
+    // the wait for the step kernel (record 0 exists whenever there are iolet sites)
+    L[e] = links[c[e] <= -2 ? -c[e] - 2 : 0];
+    a[e] = BC<R>::amp(p, amp, L[e].kind == 0 && L[e].group >= 0 ? L[e].group : 0);
+  }
   pdl_wait();
   pdl_trigger();
   const int64_t n = p.n;
   // s'_ibar(x): the value in the slot the link of direction i reads
-  auto slot_of = [&](int i, int32_t c) -> int64_t {
-    return i == 0 ? x : (ODD ? aa_addr(i, c, n, x) : (int64_t)i * n + x);
-  };
-  const R v0 = to_real(A[slot_of(i0, c0)]);
-  const R v1 = two ? to_real(A[slot_of(i1, c1)]) : R(0);
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int i = e * W + hl;
+    v[e] = R(0);
+    if (i < Q) v[e] = to_real(A[i == 0 ? x : (ODD ? aa_addr(i, c[e], n, x) : (int64_t)i * n + x)]);
+  }
   // rho = 1 + sum s'_k, j = sum s'_k c_k in direction order; s'_k sits with direction opp(k)
   R d = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     const int o = opp(k);
-    const R vk = __shfl_sync(FULL_MASK, o < 16 ? v0 : v1, o & 15, 16);
+    const R vk = __shfl_sync(FULL_MASK, v[o / W], o % W, W);
     d += vk;
     if (cx(k)) jx += cx(k) > 0 ? vk : -vk;
     if (cy(k)) jy += cy(k) > 0 ? vk : -vk;
@@ -554,15 +569,14 @@ __global__ void __launch_bounds__(256, 8) k_aa_fix(S* A, const int32_t* __restri
   const R rho = R(1) + d;
   const R ux = jx / rho, uy = jy / rho, uz = jz / rho;
   if (!live) return;
-  if (c0 <= -2) {
-    const R val = lane_iolet_value<R>(i0, L0, v0, rho, ux, uy, uz, a0, p);
-    lflux[-c0 - 2] = (double)val - (double)v0;
-    A[(int64_t)i0 * n + x] = from_real<S>(val);
-  }
-  if (c1 <= -2) {
-    const R val = lane_iolet_value<R>(i1, L1, v1, rho, ux, uy, uz, a1, p);
-    lflux[-c1 - 2] = (double)val - (double)v1;
-    A[(int64_t)i1 * n + x] = from_real<S>(val);
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const int i = e * W + hl;
+    if (c[e] <= -2) {
+      const R val = lane_iolet_value<R>(i, L[e], v[e], rho, ux, uy, uz, a[e], p);
+      lflux[-c[e] - 2] = (double)val - (double)v[e];
+      A[(int64_t)i * n + x] = from_real<S>(val);
+    }
   }
 }
 
@@ -895,7 +909,8 @@ cudaError_t dispatch(int precision, A... a) {
 template <typename S>
 cudaError_t launch_gather(const hlb_solver* h, const void* fin, void* fout, const StepParams& p, uint32_t tile0,
                           uint32_t ntiles, bool iolets, cudaStream_t s) {
-  const unsigned gi = iolets ? (unsigned)((h->n_iolet_sites + 15) / 16) : 0u;  // 16 half-warps (sites) per block
+  constexpr unsigned per_block = BLOCK / kStepIoletLanes;  // iolet sites a block
+  const unsigned gi = iolets ? (unsigned)((h->n_iolet_sites + per_block - 1) / per_block) : 0u;
   const unsigned grid = gi + ntiles;
   if (grid == 0) return cudaSuccess;
   if constexpr (sizeof(S) <= 4) {
@@ -963,7 +978,8 @@ struct AAOp {
     else
       e = aa_even<S>(h, (S*)A, p, s);
     if (e != cudaSuccess || h->n_iolet_sites == 0) return e;
-    const unsigned g = (unsigned)((h->n_iolet_sites + 15) / 16);  // one half-warp per iolet site
+    constexpr int per_block = 256 / kFixLanes;  // iolet sites a block
+    const unsigned g = (unsigned)((h->n_iolet_sites + per_block - 1) / per_block);
     return launch_pdl(odd ? k_aa_fix<S, true> : k_aa_fix<S, false>, g, 256, s, (S*)A, h->d_icode, h->d_links,
                       h->d_amp, h->d_iolet_sites, h->n_iolet_sites, p, h->d_lflux);
   }
