@@ -717,6 +717,9 @@ def main():
                     help="skip the adjoint run that keeps whole segments in most of the free device memory")
     ap.add_argument("--split-kernels", action="store_true",
                     help="the paper's per-site-type kernels on streams against the fused kernel (FP32 pull A-B)")
+    ap.add_argument("--precision-only", action="store_true",
+                    help="only the storage forms' u and WSS error against the FP64 oracle "
+                         "(--precision-sites, --precision-steps)")
     ap.add_argument("--precision-study", action="store_true",
                     help="u and WSS error of FP32/BF16/FP16 storage vs FP64 at 1k, 5k, 10k steps")
     ap.add_argument("--ref-budget", type=float, default=150.0,
@@ -745,6 +748,11 @@ def main():
         print(json.dumps({"precision_study": res, "n_sites": lat.n, "workload": WORKLOAD,
                           "reference": "GPU FP64 storage and arithmetic (equal to the FP64 oracle to rounding "
                                        "in the parity tests)"}))
+    elif args.precision_only:
+        import torch
+        torch.cuda.set_device(0)
+        errs, info = precision_vs_oracle(args.precision_sites, args.precision_steps, torch)
+        print(json.dumps({"precision_vs_oracle": dict(info, forms=errs)}))
     elif args.split_kernels:
         import torch
         torch.cuda.set_device(0)
